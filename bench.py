@@ -1,0 +1,356 @@
+"""Benchmark: RK4 grid-point-steps/s of the pseudo-spectral Navier-Stokes
+solver (Mortensen, EuroSciPy 2015, Sec. 2) on GB300.
+
+Workload (default): decaying isotropic turbulence on a 512^3 mesh, random-
+phase solenoidal initial field with E(k) ~ k^4 exp(-2 (k/4)^2) at unit
+energy, nu = 1/4000, CFL-0.5 time step, 2/3-rule dealiasing, FP32.  A step
+is one classical RK4 step (4 right-hand sides).  Inputs (several GB) are far
+larger than L2, so no L2 flush is needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  For --gpus N > 1 (launched by torchrun) every
+rank advances its own independent box (replicas; weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "RK4 grid-point-steps/s at 512^3, FP32 vs FP64, % of HBM roofline"
+SEED = 2024
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--N", type=int, default=512)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-fp64", action="store_true")
+    return p.parse_args()
+
+
+def workload(N):
+    from paper_1607_00850_gb300 import inputs
+    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
+    dt = inputs.cfl_dt(uh, 0.5)
+    return uh, 1.0 / 4000.0, dt
+
+
+def config(N, dt):
+    return {"workload": f"decaying isotropic turbulence {N}^3, E(k)~k^4 exp(-2(k/4)^2), unit energy, "
+                        f"nu=1/4000, CFL-0.5 dt, 2/3 dealiasing, classical RK4",
+            "N": N, "nu": 1.0 / 4000.0, "dt": dt, "seed": SEED,
+            "l2": "inputs larger than L2 (working set several GB); no flush"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = [r for r in self.rows if len(r) >= 9]
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_max": max((float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                                   default=None)}
+
+
+def pass_bytes(N, dtype, stage):
+    """Algorithmic HBM bytes of each pass of one RK4 stage of the pruned
+    design (K = floor((N-1)/3), Kx = 2K+1, Kz = K+1): every stored mode or
+    intermediate value is read once and written once."""
+    K = (N - 1) // 3
+    Kx, Kz = 2 * K + 1, K + 1
+    cr = 16 if dtype == 1 else 8           # field complex bytes
+    ca = 8 if dtype == 0 else 16           # accumulator complex bytes
+    S = 3 * Kx * Kx * Kz                   # state elements (3 components)
+    p1 = 3 * Kx * Kx * Kz * cr + 6 * N * Kx * Kz * cr
+    p2 = 6 * N * Kx * Kz * cr + 6 * N * N * Kz * cr
+    p3 = 6 * N * N * Kz * cr + 3 * N * N * Kz * cr
+    p4 = 3 * N * N * Kz * cr + 3 * N * Kx * Kz * cr
+    same = cr == ca
+    rd = 3 * N * Kx * Kz * cr + S * cr                 # N^ after y, stage input (viscous term)
+    if stage < 3 and not (same and stage == 0):
+        rd += S * ca                                   # u0
+    if stage > 0:
+        rd += S * ca                                   # u1
+    wr = 0
+    if stage < 3:
+        wr += S * ca + S * cr                          # u1, next stage input
+    else:
+        wr += S * ca + (0 if same else S * cr)         # u0 (and the field copy)
+    return [p1, p2, p3, p4, rd + wr]
+
+
+def survey_step_bytes(N, dtype):
+    """The unpruned reference byte model: 216 spectral-field passes per RK4
+    step, one field F = N^2 (N/2+1) complex."""
+    cr = 16 if dtype == 1 else 8
+    return 216 * N * N * (N // 2 + 1) * cr
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    from paper_1607_00850_gb300 import build, dns
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    dns.load()
+    N = args.N
+    uh, nu, dt = workload(N)
+    cfg = config(N, dt)
+    stream = torch.cuda.Stream()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    u32 = uh.astype(np.complex64)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    s = dns.Solver(N, nu, dt, dns.DNS_F32, stream=stream.cuda_stream)
+    s.set_velocity(u32)
+    E0 = s.energy()
+    s.step(args.warmup)
+    s.synchronize()
+    # ---- timed region: graph replay of K steps
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    s.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    # ---- per-kernel durations: K plain-launched steps with events on the same stream
+    pass_ms, prof_total = dns.dns_step_profiled(s.h, args.steps)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    steps_done = args.warmup + 2 * args.steps
+    E32 = s.energy()
+    s.close()
+
+    value = world * float(N) ** 3 * args.steps / (ms / 1e3)
+    peak, peak_src = measured_peaks()
+    launches = 4 * args.steps
+    per_stage = [pass_bytes(N, 0, st) for st in range(4)]
+    avg_bytes = [sum(p[i] for p in per_stage) / 4 for i in range(5)]
+    names = ["p1_curl_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5_xfwd_update"]
+    dom = int(np.argmax(pass_ms))
+    dur = pass_ms[dom] / launches
+    achieved = avg_bytes[dom] / (dur / 1e3) / 1e9
+    step_bytes = sum(sum(p) for p in per_stage)
+    roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "algorithmic_bytes_per_launch": avg_bytes[dom], "avg_launch_ms": dur,
+                "step_bytes_pruned": step_bytes,
+                "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
+                "step_bytes_216F_model": survey_step_bytes(N, 0),
+                "step_frac_216F_model": survey_step_bytes(N, 0) / (ms / args.steps / 1e3) / 1e9 / peak,
+                "pass_ms_per_launch": {names[i]: pass_ms[i] / launches for i in range(5)},
+                "pass_share": {names[i]: pass_ms[i] / max(prof_total, 1e-9) for i in range(5)}}
+
+    # ---- end to end through the C ABI with host buffers
+    hin = torch.from_numpy(u32).pin_memory()
+    hout = torch.empty_like(hin).pin_memory()
+    s = dns.Solver(N, nu, dt, dns.DNS_F32, stream=stream.cuda_stream)
+    s.set_velocity(hin)
+    s.step(1)
+    s.get_velocity(hout)
+    barrier()
+    ke = max(1, min(args.steps, 5))
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        s.set_velocity(hin)          # H2D of the step's input from pinned memory
+        s.step(1)
+        s.get_velocity(hout)         # D2H of the step's result
+    t1 = time.perf_counter()
+    s.close()
+    e2e_s = t1 - t0
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    nbytes = int(hin.numel() * hin.element_size())
+    e2e = {"value": world * float(N) ** 3 * ke / e2e_s, "unit": "grid-point-steps/s",
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke}
+
+    # ---- FP64 and mixed precision side by side (same workload, fewer steps)
+    extra = {}
+    if not args.no_fp64:
+        for name, dtype in (("fp64", dns.DNS_F64), ("f32_acc64", dns.DNS_F32_ACC64)):
+            s = dns.Solver(N, nu, dt, dtype, stream=stream.cuda_stream)
+            s.set_velocity(uh)
+            k64 = max(1, min(args.steps, 3))
+            s.step(1)
+            s.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            s.step(k64)
+            b.record(stream)
+            b.synchronize()
+            m64 = a.elapsed_time(b)
+            s.step(steps_done - 1 - k64)
+            E = s.energy()
+            s.close()
+            extra[name] = {"value": float(N) ** 3 * k64 / (m64 / 1e3), "ms_per_step": m64 / k64,
+                           "steps_timed": k64, "energy_after_steps": E}
+        Eref = extra["fp64"]["energy_after_steps"]
+        extra["fp32_energy_rel_err_vs_fp64"] = abs(E32 - Eref) / Eref
+        extra["energy_steps"] = steps_done
+    del uh
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(N, nu)
+    line = {"metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded random-phase isotropic field)", "config": cfg,
+            "parallelism": "replicas" if world > 1 else "single GPU",
+            "gpu_launches": 20 * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "cpu_baseline": cpu, "energy": {"initial": E0, "after_steps": E32}, **extra}
+    return line
+
+
+def cpu_baseline(N, nu):
+    """The FP64 oracle, as it stands, on the host cores: one right-hand side
+    evaluation (a quarter of an RK4 step) on the same field."""
+    import oracle
+    from paper_1607_00850_gb300 import inputs
+    o = oracle.load()
+    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
+    t0 = time.perf_counter()
+    o.rhs(uh, nu)
+    t = time.perf_counter() - t0
+    return {"value": float(N) ** 3 / (4 * t), "unit": "grid-point-steps/s", "cores": o.num_threads(),
+            "kind": "oracle", "sample": f"one right-hand side at {N}^3 (1/4 RK4 step), {t:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores on this workload: each step is one
+    right-hand-side evaluation at N^3 (a bounded quarter of an RK4 step)."""
+    import oracle
+    from paper_1607_00850_gb300 import inputs
+    o = oracle.load()
+    N = args.N
+    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
+    dt = inputs.cfl_dt(uh, 0.5)
+    o.rhs(inputs.random_isotropic(32, seed=1), 1e-3)   # warm the code once, small
+    budget = 150.0
+    t0 = time.perf_counter()
+    n = 0
+    while n < max(1, args.steps):
+        o.rhs(uh, 1.0 / 4000.0)
+        n += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    t = time.perf_counter() - t0
+    value = float(N) ** 3 * n / (4 * t)
+    cores = o.num_threads()
+    sample = f"{n} right-hand sides at {N}^3 (each 1/4 RK4 step), {t:.1f} s"
+    return {"metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": world, "steps": n,
+            "warmup": 1, "ms_per_step": 4 * t / n * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-phase isotropic field)",
+            "config": config(N, dt), "impl": "reference",
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value,
+                             "unit": "grid-point-steps/s"},
+            "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args, rank, world)), flush=True)
+        return 0
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,141 @@
+/*
+ * libdns: single-GPU pseudo-spectral Navier-Stokes solver (GB300, sm_103a).
+ *
+ * Method: Mortensen, "Massively parallel implementation in Python of a
+ * pseudo-spectral DNS code for turbulent flows" (EuroSciPy 2015), Sec. 2:
+ * triply periodic box [0, 2 pi]^3 on an N^3 mesh (Eq. realmesh), wavenumbers
+ * k in {-N/2+1, ..., N/2}^3 (Eq. wavemesh), transform pair of Eq. ffteq
+ * (forward unnormalised, inverse 1/N^3), right-hand side of Eq. NSfinal in
+ * rotational form
+ *     d uhat/dt = P[ m(k) (u x omega)^ ] - nu |k|^2 uhat,
+ *     P = I - k k^T / |k|^2   (pressure eliminated, Eq. pressure),
+ * with the 2/3-rule mask m(k) = [3|kx| < N and 3|ky| < N and 3|kz| < N]
+ * and the classical fourth-order Runge-Kutta integrator (end of Sec. 2).
+ *
+ * Conventions shared by every entry point:
+ *  - Every function returns an int status (dns_status); nothing throws.
+ *  - One handle is used by one host thread at a time.
+ *  - The handle owns all device memory it needs; it is allocated by
+ *    dns_init and released by dns_free.  Caller buffers are never retained:
+ *    the library copies in or out before returning (or, for device buffers,
+ *    in stream order on the handle's stream).
+ *  - `on_device` = 1: the pointer is device memory (e.g. a torch CUDA
+ *    tensor's data_ptr()); 0: host memory (pinned or pageable).
+ *  - Spectral layout ("full"): uhat[3][N][N][N/2+1] complex, C order,
+ *    interleaved (re, im); kx and ky in FFT order 0..N/2, -N/2+1..-1, kz =
+ *    0..N/2.  Physical layout: u[3][N][N][N] real, z fastest, x_i = 2 pi i/N.
+ *  - I/O element type: DNS_F32 -> complex64 / float32;
+ *    DNS_F64 and DNS_F32_ACC64 -> complex128 / float64.
+ *  - The state lives in the dealiased set: modes with 3|k_i| >= N are not
+ *    stored.  Inputs are projected onto that set on entry (such modes are
+ *    ignored); outputs carry exact zeros there.  For inputs that are already
+ *    dealiased (every field this library produces) this is Eq. NSfinal
+ *    exactly, because its right-hand side never leaves the set.
+ *  - Inputs must be Hermitian on the kz = 0 plane (real fields); the kz = 0
+ *    modes enter the inverse transform through their real part only, as in
+ *    the usual inverse real FFT.
+ */
+#ifndef DNS_H
+#define DNS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dns_ctx *dns_handle;
+
+/* Arithmetic of the path.
+ * DNS_F32:       every field and transform in float.
+ * DNS_F64:       every field and transform in double.
+ * DNS_F32_ACC64: transforms and right-hand side in float; the RK4 start and
+ *                accumulator states (u0, u1) in double.
+ * Diagnostics always accumulate in double. */
+enum dns_dtype { DNS_F32 = 0, DNS_F64 = 1, DNS_F32_ACC64 = 2 };
+
+enum dns_status {
+    DNS_OK = 0,
+    DNS_ERR_ARG = 1,         /* bad pointer, size or value */
+    DNS_ERR_OOM = 2,         /* device or host allocation failed */
+    DNS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
+    DNS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
+    DNS_ERR_NONFINITE = 5,   /* NaN or Inf found in the state */
+    DNS_ERR_UNSUPPORTED = 6  /* N, dtype or option not supported */
+};
+
+/* Create a solver for an N^3 box.  N: even, 8 <= N <= 1024, N = 2^a or
+ * 3 * 2^a (else DNS_ERR_UNSUPPORTED).  nu > 0 viscosity, dt > 0 time step.
+ * cuda_stream: a cudaStream_t to run on, or NULL for a stream the handle
+ * creates.  The velocity starts at zero, t = 0, step = 0.
+ * Errors: DNS_ERR_ARG, DNS_ERR_UNSUPPORTED, DNS_ERR_OOM, DNS_ERR_CUDA. */
+int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_handle *out);
+
+/* Release the handle and its device memory.  NULL is accepted. */
+int dns_free(dns_handle h);
+
+/* Set the state from a full spectral field (layout and type above).
+ * Synchronous with respect to the host buffer.  Does not change t or step. */
+int dns_set_velocity(dns_handle h, const void *uhat, int on_device);
+
+/* Set the state from a physical field u[3][N][N][N] (I/O real type), by the
+ * forward transform of Eq. ffteq followed by the dealiasing mask. */
+int dns_set_velocity_physical(dns_handle h, const void *u, int on_device);
+
+/* Copy the state out as a full spectral field (zeros outside the dealiased
+ * set).  Synchronises the handle's stream. */
+int dns_get_velocity(dns_handle h, void *uhat, int on_device);
+
+/* One evaluation of the right-hand side of Eq. NSfinal on uhat_in (full
+ * layout), written to duhat_out (full layout).  Leaves the state unchanged.
+ * Synchronises the handle's stream. */
+int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device);
+
+/* Advance n >= 0 classical RK4 steps.  Asynchronous: work is queued on the
+ * handle's stream (as replays of a CUDA graph of one step, captured on the
+ * first call); errors from the device surface at the next synchronising
+ * call.  Not to be called while the handle's stream is being captured. */
+int dns_step(dns_handle h, int n);
+
+/* Advance n steps with plain kernel launches and CUDA events around every
+ * launch, and add the device time of each pass to pass_ms[0..4]:
+ * [0] inverse x transform + curl, [1] inverse y transform,
+ * [2] z transforms + cross product, [3] forward y transform,
+ * [4] forward x transform + dealias + projection + viscous term + RK4.
+ * total_ms receives the device time from the first launch to the last.
+ * Synchronises the handle's stream. */
+int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms);
+
+/* Wait for the handle's queued work; reports device errors. */
+int dns_synchronize(dns_handle h);
+
+/* Diagnostics of the current state, accumulated in double (synchronising):
+ * E = <|u|^2>/2, eps = nu <|grad u|^2>, and the shell spectrum
+ * Ek[s] = sum over modes with floor(|k| + 1/2) = s of |uhat|^2 / (2 N^6)
+ * (half-spectrum modes with kz > 0 counted twice).  nshells >= 1; shells
+ * beyond nshells-1 are dropped.  A non-finite E or eps returns
+ * DNS_ERR_NONFINITE (the value is still written). */
+int dns_energy(dns_handle h, double *E);
+int dns_dissipation(dns_handle h, double *eps);
+int dns_spectrum(dns_handle h, double *Ek, int nshells);
+
+/* Simulated time and step count; dns_set_time restores them on resume. */
+int dns_time(dns_handle h, double *t, long *step);
+int dns_set_time(dns_handle h, double t, long step);
+
+/* Handle parameters: N, dtype, and the largest kept wavenumber
+ * kmax = floor((N-1)/3).  Any output pointer may be NULL. */
+int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *dt);
+
+/* Bytes of device memory the handle holds. */
+int dns_device_bytes(dns_handle h, long long *bytes);
+
+/* Human-readable name of a status code (static storage). */
+const char *dns_strerror(int status);
+
+/* Text of the last CUDA runtime error this thread saw inside the library
+ * (static storage; "no error" if none). */
+const char *dns_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

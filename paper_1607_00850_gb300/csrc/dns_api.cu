@@ -1,0 +1,546 @@
+// C-ABI of the single-GPU pseudo-spectral solver (include/dns.h).
+//
+// One RK4 step = 4 stages x 5 passes (dns_passes.cuh).  The step is captured
+// once into a CUDA graph and replayed.  All buffers are allocated at
+// dns_init; nothing is allocated on the stepping path.
+#include "dns.h"
+#include "dns_internal.h"
+#include "dns_passes.cuh"
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace dns {
+#define DNS_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512) X(768) X(1024)
+#define DNS_DECL(n) bool get_passes_##n(int, PassSet *);
+DNS_SIZES(DNS_DECL)
+#undef DNS_DECL
+
+static PassGetter getter_for(int N) {
+    switch (N) {
+#define DNS_CASE(n) \
+    case n:         \
+        return get_passes_##n;
+        DNS_SIZES(DNS_CASE)
+#undef DNS_CASE
+        default:
+            return nullptr;
+    }
+}
+}  // namespace dns
+
+using dns::Geo;
+
+struct dns_ctx {
+    int N = 0, dtype = 0;
+    double nu = 0, dt = 0, t = 0;
+    long step = 0;
+    Geo g{};
+    dns::PassSet ps{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    bool same_type = false;   // field and accumulator types coincide
+    size_t creal = 0, cacc = 0, cio = 0;  // bytes per complex element
+    void *U = nullptr, *U0 = nullptr, *U1 = nullptr, *A = nullptr, *B = nullptr;
+    void *io = nullptr, *rin = nullptr, *rout = nullptr, *tw = nullptr;
+    double *partials = nullptr, *sums = nullptr, *Ek = nullptr;
+    int nblk = 0, smax = 0;
+    double *host = nullptr;  // pinned read-back area
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    long long bytes = 0;
+};
+
+static thread_local cudaError_t g_last_cuda = cudaSuccess;
+
+#define CK(call)                              \
+    do {                                      \
+        cudaError_t e_ = (call);              \
+        if (e_ != cudaSuccess) {              \
+            g_last_cuda = e_;                 \
+            return DNS_ERR_CUDA;              \
+        }                                     \
+    } while (0)
+
+static const double RK_A[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
+static const double RK_B[3] = {0.5, 0.5, 1.0};
+
+static void release(dns_ctx *h) {
+    if (!h) return;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    void *bufs[] = {h->U, h->U0, h->U1, h->A, h->B, h->io, h->rin, h->rout, h->tw, h->partials, h->sums, h->Ek};
+    for (void *p : bufs)
+        if (p) cudaFree(p);
+    if (h->host) cudaFreeHost(h->host);
+    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    delete h;
+}
+
+static int dev_alloc(dns_ctx *h, void **p, size_t bytes) {
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return DNS_ERR_OOM;
+    }
+    h->bytes += (long long)bytes;
+    return DNS_OK;
+}
+
+static inline int grid_for(long long total) {
+    long long b = (total + 255) / 256;
+    return (int)(b < 4864 ? (b < 1 ? 1 : b) : 4864);
+}
+
+// --------------------------------------------------------------- conversions
+template <typename Tin, typename Tout>
+static cudaError_t to_compact(const dns_ctx *h, const void *full, void *cmp) {
+    const long long total = 3LL * h->g.Kx * h->g.Kx * h->g.Kz;
+    dns::k_full_to_compact<Tin, Tout><<<grid_for(total), 256, 0, h->stream>>>(h->g, (const Tin *)full, (Tout *)cmp);
+    return cudaGetLastError();
+}
+template <typename Tin, typename Tout>
+static cudaError_t to_full(const dns_ctx *h, const void *cmp, void *full) {
+    const long long total = 3LL * h->N * h->N * (h->N / 2 + 1);
+    dns::k_compact_to_full<Tin, Tout><<<grid_for(total), 256, 0, h->stream>>>(h->g, (const Tin *)cmp, (Tout *)full);
+    return cudaGetLastError();
+}
+
+// elementwise copy between compact buffers of different complex types
+template <typename Tin, typename Tout>
+__global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ b, long long n) {
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        Tout o;
+        o.x = a[e].x;
+        o.y = a[e].y;
+        b[e] = o;
+    }
+}
+
+// full (io type) -> compact (real type) and compact (acc type)
+static cudaError_t full_to_state(dns_ctx *h, const void *full, void *dst_real, void *dst_acc) {
+    cudaError_t e = cudaSuccess;
+    if (h->dtype == DNS_F32) {
+        if (dst_real) e = to_compact<float2, float2>(h, full, dst_real);
+        if (e == cudaSuccess && dst_acc) e = to_compact<float2, float2>(h, full, dst_acc);
+    } else if (h->dtype == DNS_F64) {
+        if (dst_real) e = to_compact<double2, double2>(h, full, dst_real);
+        if (e == cudaSuccess && dst_acc) e = to_compact<double2, double2>(h, full, dst_acc);
+    } else {
+        if (dst_real) e = to_compact<double2, float2>(h, full, dst_real);
+        if (e == cudaSuccess && dst_acc) e = to_compact<double2, double2>(h, full, dst_acc);
+    }
+    return e;
+}
+
+// compact (acc type) -> full (io type); io type == acc type in every mode
+static cudaError_t acc_to_full(dns_ctx *h, const void *cmp, void *full) {
+    if (h->dtype == DNS_F32) return to_full<float2, float2>(h, cmp, full);
+    return to_full<double2, double2>(h, cmp, full);
+}
+
+// --------------------------------------------------------------- the path
+static cudaError_t launch_front(dns_ctx *h, const void *Uin) {
+    cudaError_t e;
+    const double scale = 1.0 / ((double)h->N * h->N * h->N);
+    if ((e = h->ps.p1(h->g, h->tw, Uin, h->A, scale, h->stream)) != cudaSuccess) return e;
+    if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+    if ((e = h->ps.p3(h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
+    return h->ps.p4(h->g, h->tw, h->B, h->A, h->stream);
+}
+
+static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
+    dns::UpdateArgsErased a{};
+    a.U = (s == 0 && h->same_type) ? h->U0 : h->U;
+    a.U0 = h->U0;
+    a.U1 = h->U1;
+    a.Uout = (s < 3 || !h->same_type) ? h->U : nullptr;
+    a.U0out = (s == 3) ? h->U0 : nullptr;
+    a.dU = nullptr;
+    a.nu = h->nu;
+    a.adt = RK_A[s] * h->dt;
+    a.bdt = s < 3 ? RK_B[s] * h->dt : 0.0;
+    a.stage = s;
+    return a;
+}
+
+// Enqueue one RK4 step; if ev != nullptr record ev[1 + i] after launch i.
+static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
+    cudaError_t e;
+    int li = 0;
+    auto mark = [&]() -> cudaError_t {
+        if (!ev) return cudaSuccess;
+        return cudaEventRecord(ev[++li], h->stream);
+    };
+    const double scale = 1.0 / ((double)h->N * h->N * h->N);
+    for (int s = 0; s < 4; ++s) {
+        dns::UpdateArgsErased a = stage_args(h, s);
+        if ((e = h->ps.p1(h->g, h->tw, a.U, h->A, scale, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = h->ps.p3(h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = h->ps.p4(h->g, h->tw, h->B, h->A, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = h->ps.p5(h->g, h->tw, h->A, a, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// --------------------------------------------------------------- API
+extern "C" {
+
+const char *dns_strerror(int status) {
+    switch (status) {
+        case DNS_OK: return "ok";
+        case DNS_ERR_ARG: return "invalid argument";
+        case DNS_ERR_OOM: return "out of memory";
+        case DNS_ERR_CUDA: return "CUDA error";
+        case DNS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DNS_ERR_NONFINITE: return "non-finite value in the state";
+        case DNS_ERR_UNSUPPORTED: return "unsupported size, dtype or option";
+        default: return "unknown status";
+    }
+}
+
+const char *dns_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
+
+int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_handle *out) {
+    if (!out) return DNS_ERR_ARG;
+    *out = nullptr;
+    if (dtype < DNS_F32 || dtype > DNS_F32_ACC64) return DNS_ERR_ARG;
+    if (!(nu > 0.0) || !(dt > 0.0) || !std::isfinite(nu) || !std::isfinite(dt)) return DNS_ERR_ARG;
+    dns::PassGetter get = dns::getter_for(N);
+    if (!get) return DNS_ERR_UNSUPPORTED;
+    dns_ctx *h = new (std::nothrow) dns_ctx();
+    if (!h) return DNS_ERR_OOM;
+    h->N = N;
+    h->dtype = dtype;
+    h->nu = nu;
+    h->dt = dt;
+    if (!get(dtype, &h->ps)) {
+        delete h;
+        return DNS_ERR_UNSUPPORTED;
+    }
+    const int K = (N - 1) / 3;
+    Geo &g = h->g;
+    g.N = N;
+    g.K = K;
+    g.Kx = 2 * K + 1;
+    g.Kz = K + 1;
+    g.Kzp = (g.Kz + 3) / 4 * 4;
+    g.sS = (long long)g.Kx * g.Kx * g.Kzp;
+    g.sA = (long long)N * g.Kx * g.Kzp;
+    g.sB = (long long)N * N * g.Kzp;
+    h->creal = dtype == DNS_F64 ? 16 : 8;
+    h->cacc = dtype == DNS_F32 ? 8 : 16;
+    h->cio = h->cacc;
+    h->same_type = h->creal == h->cacc;
+    int rc = DNS_OK;
+    const size_t nfull = 3ull * N * N * (N / 2 + 1);
+    h->nblk = 2 * 152;
+    h->smax = (int)std::floor(std::sqrt(3.0) * K + 0.5) + 1;
+    if (!rc) rc = dev_alloc(h, &h->U, 3 * g.sS * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->U0, 3 * g.sS * h->cacc);
+    if (!rc) rc = dev_alloc(h, &h->U1, 3 * g.sS * h->cacc);
+    if (!rc) rc = dev_alloc(h, &h->A, 6 * g.sA * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->B, 6 * g.sB * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->io, nfull * h->cio);
+    if (!rc) rc = dev_alloc(h, &h->rin, 3 * g.sS * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->rout, 3 * g.sS * h->cacc);
+    if (!rc) rc = dev_alloc(h, &h->tw, (size_t)N * h->creal);
+    if (!rc) rc = dev_alloc(h, (void **)&h->partials, sizeof(double) * 2 * h->nblk);
+    if (!rc) rc = dev_alloc(h, (void **)&h->sums, sizeof(double) * 2);
+    if (!rc) rc = dev_alloc(h, (void **)&h->Ek, sizeof(double) * h->smax);
+    if (!rc && cudaMallocHost((void **)&h->host, sizeof(double) * (4 + h->smax)) != cudaSuccess) {
+        h->host = nullptr;
+        rc = DNS_ERR_OOM;
+    }
+    if (rc) {
+        release(h);
+        return rc;
+    }
+    if (cuda_stream) {
+        h->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreate(&h->stream) != cudaSuccess) {
+            h->stream = nullptr;
+            release(h);
+            return DNS_ERR_CUDA;
+        }
+        h->own_stream = true;
+    }
+    // twiddles w[m] = exp(-2 pi i m / N), built in double
+    std::vector<double> twd(2 * (size_t)N);
+    for (int m = 0; m < N; ++m) {
+        const double a = 2.0 * M_PI * (double)m / (double)N;
+        twd[2 * m] = std::cos(a);
+        twd[2 * m + 1] = -std::sin(a);
+    }
+    cudaError_t e = cudaSuccess;
+    if (h->creal == 8) {
+        std::vector<float> twf(2 * (size_t)N);
+        for (size_t i = 0; i < twf.size(); ++i) twf[i] = (float)twd[i];
+        e = cudaMemcpy(h->tw, twf.data(), twf.size() * sizeof(float), cudaMemcpyHostToDevice);
+    } else {
+        e = cudaMemcpy(h->tw, twd.data(), twd.size() * sizeof(double), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, 3 * g.sS * h->creal, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, 3 * g.sS * h->cacc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, 3 * g.sS * h->cacc, h->stream);
+    if (e == cudaSuccess) e = h->ps.prepare();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        release(h);
+        return DNS_ERR_CUDA;
+    }
+    *out = h;
+    return DNS_OK;
+}
+
+int dns_free(dns_handle h) {
+    if (!h) return DNS_OK;
+    cudaStreamSynchronize(h->stream);
+    release(h);
+    return DNS_OK;
+}
+
+int dns_synchronize(dns_handle h) {
+    if (!h) return DNS_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+int dns_set_velocity(dns_handle h, const void *uhat, int on_device) {
+    if (!h || !uhat) return DNS_ERR_ARG;
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    const void *src = uhat;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->io, uhat, bytes, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+    }
+    CK(full_to_state(h, src, h->U, h->U0));
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
+    if (!h || !u) return DNS_ERR_ARG;
+    const size_t nreal = 3ull * h->N * h->N * h->N;
+    const size_t bytes = nreal * (h->cio / 2);
+    const void *src = u;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->io, u, bytes, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+    }
+    CK(h->ps.zfwd(h->g, h->tw, src, h->B, h->stream));
+    CK(h->ps.p4(h->g, h->tw, h->B, h->A, h->stream));
+    dns::UpdateArgsErased a{};
+    a.dU = h->rout;
+    a.stage = -2;
+    CK(h->ps.p5(h->g, h->tw, h->A, a, h->stream));
+    const long long n = 3 * h->g.sS;
+    CK(cudaMemcpyAsync(h->U0, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
+    if (h->same_type) {
+        CK(cudaMemcpyAsync(h->U, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
+    } else {
+        k_convert<double2, float2><<<grid_for(n), 256, 0, h->stream>>>((const double2 *)h->rout, (float2 *)h->U, n);
+        CK(cudaGetLastError());
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+int dns_get_velocity(dns_handle h, void *uhat, int on_device) {
+    if (!h || !uhat) return DNS_ERR_ARG;
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    if (on_device) {
+        CK(acc_to_full(h, h->U0, uhat));
+    } else {
+        CK(acc_to_full(h, h->U0, h->io));
+        CK(cudaMemcpyAsync(uhat, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
+    if (!h || !uhat_in || !duhat_out) return DNS_ERR_ARG;
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    const void *src = uhat_in;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->io, uhat_in, bytes, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+    }
+    CK(full_to_state(h, src, h->rin, nullptr));
+    CK(launch_front(h, h->rin));
+    dns::UpdateArgsErased a{};
+    a.U = h->rin;
+    a.dU = h->rout;
+    a.nu = h->nu;
+    a.stage = -1;
+    CK(h->ps.p5(h->g, h->tw, h->A, a, h->stream));
+    if (on_device) {
+        CK(acc_to_full(h, h->rout, duhat_out));
+    } else {
+        CK(acc_to_full(h, h->rout, h->io));
+        CK(cudaMemcpyAsync(duhat_out, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+int dns_step(dns_handle h, int n) {
+    if (!h || n < 0) return DNS_ERR_ARG;
+    if (n == 0) return DNS_OK;
+    if (!h->exec) {
+        CK(cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t e = enqueue_step(h, nullptr);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(h->stream, &graph);
+        if (e != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            g_last_cuda = e != cudaSuccess ? e : e2;
+            cudaGetLastError();
+            return DNS_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            g_last_cuda = e;
+            return DNS_ERR_CUDA;
+        }
+        h->graph = graph;
+        h->exec = exec;
+    }
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(h->exec, h->stream));
+    h->t += n * h->dt;
+    h->step += n;
+    return DNS_OK;
+}
+
+int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms) {
+    if (!h || n < 0 || !pass_ms) return DNS_ERR_ARG;
+    for (int i = 0; i < 5; ++i) pass_ms[i] = 0.0;
+    if (total_ms) *total_ms = 0.0;
+    if (n == 0) return DNS_OK;
+    const int per = 20;
+    std::vector<cudaEvent_t> ev((size_t)per * n + 1, nullptr);
+    int rc = DNS_OK;
+    for (auto &x : ev)
+        if (cudaEventCreate(&x) != cudaSuccess) {
+            x = nullptr;
+            rc = DNS_ERR_CUDA;
+        }
+    if (!rc && cudaEventRecord(ev[0], h->stream) != cudaSuccess) rc = DNS_ERR_CUDA;
+    for (int i = 0; i < n && !rc; ++i) {
+        cudaError_t e = enqueue_step(h, ev.data() + (size_t)per * i);
+        if (e != cudaSuccess) {
+            g_last_cuda = e;
+            rc = DNS_ERR_CUDA;
+        }
+    }
+    if (!rc && cudaStreamSynchronize(h->stream) != cudaSuccess) rc = DNS_ERR_CUDA;
+    if (!rc) {
+        for (size_t i = 0; i + 1 < ev.size(); ++i) {
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+            pass_ms[i % 5] += ms;
+        }
+        float tot = 0.f;
+        cudaEventElapsedTime(&tot, ev[0], ev.back());
+        if (total_ms) *total_ms = tot;
+        h->t += n * h->dt;
+        h->step += n;
+    }
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    return rc;
+}
+
+static int stats_sums(dns_handle h, double *se, double *sd) {
+    if (h->dtype == DNS_F32)
+        dns::k_energy_partials<float><<<h->nblk, 256, 0, h->stream>>>(h->g, (const float2 *)h->U0, h->partials);
+    else
+        dns::k_energy_partials<double><<<h->nblk, 256, 0, h->stream>>>(h->g, (const double2 *)h->U0, h->partials);
+    CK(cudaGetLastError());
+    dns::k_sum_partials<<<1, 32, 0, h->stream>>>(h->partials, h->nblk, 2, h->sums);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->host, h->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *se = h->host[0];
+    *sd = h->host[1];
+    return DNS_OK;
+}
+
+int dns_energy(dns_handle h, double *E) {
+    if (!h || !E) return DNS_ERR_ARG;
+    double se, sd;
+    int rc = stats_sums(h, &se, &sd);
+    if (rc) return rc;
+    const double N3 = (double)h->N * h->N * h->N;
+    *E = se / (2.0 * N3 * N3);
+    return std::isfinite(*E) ? DNS_OK : DNS_ERR_NONFINITE;
+}
+
+int dns_dissipation(dns_handle h, double *eps) {
+    if (!h || !eps) return DNS_ERR_ARG;
+    double se, sd;
+    int rc = stats_sums(h, &se, &sd);
+    if (rc) return rc;
+    const double N3 = (double)h->N * h->N * h->N;
+    *eps = h->nu * sd / (N3 * N3);
+    return std::isfinite(*eps) ? DNS_OK : DNS_ERR_NONFINITE;
+}
+
+int dns_spectrum(dns_handle h, double *Ek, int nshells) {
+    if (!h || !Ek || nshells < 1) return DNS_ERR_ARG;
+    if (h->dtype == DNS_F32)
+        dns::k_spectrum<float><<<h->smax, 256, 0, h->stream>>>(h->g, (const float2 *)h->U0, h->Ek);
+    else
+        dns::k_spectrum<double><<<h->smax, 256, 0, h->stream>>>(h->g, (const double2 *)h->U0, h->Ek);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->host, h->Ek, sizeof(double) * h->smax, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    for (int s = 0; s < nshells; ++s) Ek[s] = s < h->smax ? h->host[s] : 0.0;
+    return DNS_OK;
+}
+
+int dns_time(dns_handle h, double *t, long *step) {
+    if (!h) return DNS_ERR_ARG;
+    if (t) *t = h->t;
+    if (step) *step = h->step;
+    return DNS_OK;
+}
+
+int dns_set_time(dns_handle h, double t, long step) {
+    if (!h || !std::isfinite(t) || step < 0) return DNS_ERR_ARG;
+    h->t = t;
+    h->step = step;
+    return DNS_OK;
+}
+
+int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *dt) {
+    if (!h) return DNS_ERR_ARG;
+    if (N) *N = h->N;
+    if (dtype) *dtype = h->dtype;
+    if (kmax) *kmax = h->g.K;
+    if (nu) *nu = h->nu;
+    if (dt) *dt = h->dt;
+    return DNS_OK;
+}
+
+int dns_device_bytes(dns_handle h, long long *bytes) {
+    if (!h || !bytes) return DNS_ERR_ARG;
+    *bytes = h->bytes;
+    return DNS_OK;
+}
+
+}  // extern "C"

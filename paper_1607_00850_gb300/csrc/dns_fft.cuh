@@ -1,0 +1,211 @@
+// Tile FFT engine for the pseudo-spectral solver (sm_103a).
+//
+// A "tile" is a block of W independent lines of length N held in shared
+// memory as tile[n * ld + c] (row n = position along the transformed axis,
+// column c = line).  One thread block transforms all W lines together with a
+// self-sorting (Stockham) mixed-radix schedule: for a stage of radix R that
+// follows stages whose radices multiply to Ns, butterfly j (0 <= j < N/R)
+// of every line reads x[j + r N/R], multiplies input r by w_{Ns R}^{r (j mod
+// Ns)}, takes an R-point DFT and writes output r to
+// (j / Ns) Ns R + (j mod Ns) + r Ns.  After the last stage the line is in
+// natural order (Eq. ffteq: X[k] = sum_n x[n] exp(sign 2 pi i k n / N)).
+//
+// Consecutive threads take consecutive columns, so with 128-byte rows every
+// warp access to the tile is free of bank conflicts, and the first stage
+// (read through a Load functor, usually straight from HBM) and the last
+// stage (written through a Store functor) are coalesced along the columns.
+// Each stage keeps all of a thread's butterflies in registers between a read
+// phase and a write phase separated by __syncthreads(), so one buffer serves
+// in place.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace dns {
+
+template <typename R> struct CT;
+template <> struct CT<float> { typedef float2 t; };
+template <> struct CT<double> { typedef double2 t; };
+template <typename C> struct RealOf;
+template <> struct RealOf<float2> { typedef float t; };
+template <> struct RealOf<double2> { typedef double t; };
+
+template <typename T> __device__ __forceinline__ T cmk(double x, double y) {
+    T r;
+    r.x = (decltype(r.x))x;
+    r.y = (decltype(r.y))y;
+    return r;
+}
+template <typename T> __device__ __forceinline__ T cadd(T a, T b) { T r; r.x = a.x + b.x; r.y = a.y + b.y; return r; }
+template <typename T> __device__ __forceinline__ T csub(T a, T b) { T r; r.x = a.x - b.x; r.y = a.y - b.y; return r; }
+template <typename T> __device__ __forceinline__ T cmul(T a, T b) {
+    T r;
+    r.x = a.x * b.x - a.y * b.y;
+    r.y = a.x * b.y + a.y * b.x;
+    return r;
+}
+template <typename T> __device__ __forceinline__ T cconj(T a) { a.y = -a.y; return a; }
+// multiply by sign * i
+template <int SIGN, typename T> __device__ __forceinline__ T cmul_si(T a) {
+    T r;
+    if (SIGN > 0) { r.x = -a.y; r.y = a.x; }
+    else { r.x = a.y; r.y = -a.x; }
+    return r;
+}
+template <typename T, typename S> __device__ __forceinline__ T cscale(T a, S s) { a.x *= s; a.y *= s; return a; }
+
+// ---------------------------------------------------------------------------
+// Radix plan: N = 3^b * 2^a (b <= 1).  Radix 3 first, then radix 8 stages,
+// then a 4 or 4*4 (or a lone 2) for the remaining power of two.
+struct FftPlan {
+    int nst;
+    int r[8];
+    int ns[8];  // product of the radices of the earlier stages
+};
+
+__host__ __device__ constexpr FftPlan make_plan(int N) {
+    FftPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    int n = N;
+    if (n % 3 == 0) { p.r[p.nst++] = 3; n /= 3; }
+    int a = 0;
+    while ((1 << a) < n) ++a;
+    int q = a / 3, rem = a % 3;
+    if (rem == 1 && q == 0) {
+        p.r[p.nst++] = 2;
+    } else {
+        int n8 = (rem == 1) ? q - 1 : q;
+        for (int i = 0; i < n8; ++i) p.r[p.nst++] = 8;
+        if (rem == 1) { p.r[p.nst++] = 4; p.r[p.nst++] = 4; }
+        if (rem == 2) p.r[p.nst++] = 4;
+    }
+    int ns = 1;
+    for (int s = 0; s < p.nst; ++s) { p.ns[s] = ns; ns *= p.r[s]; }
+    return p;
+}
+
+__host__ __device__ constexpr int plan_max_radix(int N) {
+    FftPlan p = make_plan(N);
+    int m = 1;
+    for (int s = 0; s < p.nst; ++s) m = p.r[s] > m ? p.r[s] : m;
+    return m;
+}
+
+// ---------------------------------------------------------------------------
+// Small DFTs in registers: X[k] = sum_n v[n] exp(SIGN 2 pi i k n / R).
+template <int R, int SIGN, typename T> __device__ __forceinline__ void dft(T *v) {
+    typedef typename RealOf<T>::t real;
+    if constexpr (R == 2) {
+        T a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        const real h = (real)0.86602540378443864676;  // sqrt(3)/2
+        T t1 = cadd(v[1], v[2]);
+        T t2 = csub(v[0], cscale(t1, (real)0.5));
+        T t3 = cscale(csub(v[1], v[2]), (real)SIGN * h);
+        v[0] = cadd(v[0], t1);
+        v[1] = cmk<T>(t2.x - t3.y, t2.y + t3.x);
+        v[2] = cmk<T>(t2.x + t3.y, t2.y - t3.x);
+    } else if constexpr (R == 4) {
+        T s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+        T s13 = cadd(v[1], v[3]), d13 = cmul_si<SIGN>(csub(v[1], v[3]));
+        v[0] = cadd(s02, s13);
+        v[2] = csub(s02, s13);
+        v[1] = cadd(d02, d13);
+        v[3] = csub(d02, d13);
+    } else if constexpr (R == 8) {
+        T e[4] = {v[0], v[2], v[4], v[6]};
+        T o[4] = {v[1], v[3], v[5], v[7]};
+        dft<4, SIGN>(e);
+        dft<4, SIGN>(o);
+        const real c = (real)0.70710678118654752440;  // 1/sqrt(2)
+        // w^1 = (1 + SIGN i)/sqrt2, w^2 = SIGN i, w^3 = (-1 + SIGN i)/sqrt2
+        T o1 = cmk<T>((o[1].x - SIGN * o[1].y) * c, (o[1].y + SIGN * o[1].x) * c);
+        T o2 = cmul_si<SIGN>(o[2]);
+        T o3 = cmk<T>((-o[3].x - SIGN * o[3].y) * c, (SIGN * o[3].x - o[3].y) * c);
+        v[0] = cadd(e[0], o[0]);
+        v[4] = csub(e[0], o[0]);
+        v[1] = cadd(e[1], o1);
+        v[5] = csub(e[1], o1);
+        v[2] = cadd(e[2], o2);
+        v[6] = csub(e[2], o2);
+        v[3] = cadd(e[3], o3);
+        v[7] = csub(e[3], o3);
+    } else {
+        static_assert(R == 2 || R == 3 || R == 4 || R == 8, "unsupported radix");
+    }
+}
+
+// ---------------------------------------------------------------------------
+// The engine.  tw[m] = exp(-2 pi i m / N) (forward table); SIGN = +1 uses
+// its conjugate.  Load(n, c) -> value of row n of line c for the first
+// stage; Store(n, c, v) consumes row n of line c after the last stage.
+template <typename real, int N, int W, int T, int SIGN, int S = 0>
+struct TileFFT {
+    typedef typename CT<real>::t cplx;
+    template <class Load, class Store>
+    static __device__ __forceinline__ void run(cplx *tile, int ld, const cplx *tw, const Load &load,
+                                               const Store &store) {
+        constexpr FftPlan P = make_plan(N);
+        constexpr int R = P.r[S];
+        constexpr int Ns = P.ns[S];
+        constexpr int NB = N / R;
+        constexpr int TOT = NB * W;
+        constexpr int Q = (TOT + T - 1) / T;
+        constexpr bool first = (S == 0);
+        constexpr bool last = (S == P.nst - 1);
+        constexpr int TWS = N / (Ns * R);
+        cplx v[Q][R];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int c = idx % W, j = idx / W;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int n = j + r * NB;
+                    if constexpr (first) v[q][r] = load(n, c);
+                    else v[q][r] = tile[n * ld + c];
+                }
+                if constexpr (!first) {
+                    const int k = j % Ns;
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        cplx w = tw[r * k * TWS];
+                        if (SIGN > 0) w.y = -w.y;
+                        v[q][r] = cmul(v[q][r], w);
+                    }
+                }
+                dft<R, SIGN>(v[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int c = idx % W, j = idx / W;
+                const int base = (j / Ns) * Ns * R + (j % Ns);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int n = base + r * Ns;
+                    if constexpr (last) store(n, c, v[q][r]);
+                    else tile[n * ld + c] = v[q][r];
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (!last) TileFFT<real, N, W, T, SIGN, S + 1>::run(tile, ld, tw, load, store);
+    }
+};
+
+// Threads for a W-column tile so that each thread holds about QT butterflies
+// of the largest radix.
+__host__ __device__ constexpr int tile_threads(int N, int W, int QT) {
+    int t = (N * W / plan_max_radix(N) + QT - 1) / QT;
+    t = ((t + 31) / 32) * 32;
+    return t < 32 ? 32 : (t > 1024 ? 1024 : t);
+}
+
+}  // namespace dns

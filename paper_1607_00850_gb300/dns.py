@@ -1,0 +1,267 @@
+"""Thin ctypes binding of libdns (include/dns.h): argument marshalling only.
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the solver itself; all work runs in the CUDA kernels of
+libdns.so.  Buffers may be numpy arrays (host memory, on_device=0) or CUDA
+torch tensors (device memory, on_device=1).  A non-zero status raises
+DnsError.  If libdns.so has not been built this module fails loudly: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdns.so")
+
+DNS_F32, DNS_F64, DNS_F32_ACC64 = 0, 1, 2
+DTYPE_NAMES = {"f32": DNS_F32, "f64": DNS_F64, "f32_acc64": DNS_F32_ACC64}
+STATUS = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_OOM", 3: "DNS_ERR_CUDA", 4: "DNS_ERR_TIMEOUT",
+          5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED"}
+SUPPORTED_N = (8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024)
+
+# symbol -> (restype, argtypes); the complete exported surface of dns.h
+_vp, _i, _d, _dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)
+SIGNATURES = {
+    "dns_init": (_i, [_i, _d, _d, _i, _vp, ctypes.POINTER(_vp)]),
+    "dns_free": (_i, [_vp]),
+    "dns_set_velocity": (_i, [_vp, _vp, _i]),
+    "dns_set_velocity_physical": (_i, [_vp, _vp, _i]),
+    "dns_get_velocity": (_i, [_vp, _vp, _i]),
+    "dns_rhs": (_i, [_vp, _vp, _vp, _i]),
+    "dns_step": (_i, [_vp, _i]),
+    "dns_step_profiled": (_i, [_vp, _i, _dp, _dp]),
+    "dns_synchronize": (_i, [_vp]),
+    "dns_energy": (_i, [_vp, _dp]),
+    "dns_dissipation": (_i, [_vp, _dp]),
+    "dns_spectrum": (_i, [_vp, _dp, _i]),
+    "dns_time": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
+    "dns_set_time": (_i, [_vp, _d, ctypes.c_long]),
+    "dns_query": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _dp, _dp]),
+    "dns_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "dns_strerror": (ctypes.c_char_p, [_i]),
+    "dns_last_cuda_error": (ctypes.c_char_p, []),
+}
+
+
+class DnsError(RuntimeError):
+    def __init__(self, status: int, where: str, detail: str = ""):
+        self.status = status
+        super().__init__(f"{where}: {STATUS.get(status, status)}{(' (' + detail + ')') if detail else ''}")
+
+
+_LIB = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libdns.so and declare every entry point; raises if it is missing."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is not built; run __graft_entry__.build() (needs nvcc). "
+                           "There is no CPU fallback.")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def _check(rc: int, where: str):
+    if rc != 0:
+        detail = load().dns_last_cuda_error().decode() if rc == 3 else ""
+        raise DnsError(rc, where, detail)
+
+
+def _buf(x, writable: bool = False):
+    """(pointer, on_device, keepalive) for a numpy array or torch tensor."""
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"] or (writable and not x.flags["WRITEABLE"]):
+            raise ValueError("host buffer must be C-contiguous (and writable for outputs)")
+        return x.ctypes.data, 0, x
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr(), 1 if x.is_cuda else 0, x
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+# ---------------------------------------------------------------- entry points
+def dns_init(N: int, nu: float, dt: float, dtype: int = DNS_F32, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dns_init(int(N), float(nu), float(dt), int(dtype), stream or None, ctypes.byref(h)),
+           "dns_init")
+    return h.value
+
+
+def dns_free(h: int) -> None:
+    _check(load().dns_free(h), "dns_free")
+
+
+def dns_set_velocity(h: int, uhat) -> None:
+    p, dev, _keep = _buf(uhat)
+    _check(load().dns_set_velocity(h, p, dev), "dns_set_velocity")
+
+
+def dns_set_velocity_physical(h: int, u) -> None:
+    p, dev, _keep = _buf(u)
+    _check(load().dns_set_velocity_physical(h, p, dev), "dns_set_velocity_physical")
+
+
+def dns_get_velocity(h: int, out) -> None:
+    p, dev, _keep = _buf(out, writable=True)
+    _check(load().dns_get_velocity(h, p, dev), "dns_get_velocity")
+
+
+def dns_rhs(h: int, uhat_in, duhat_out) -> None:
+    pi, di, _k1 = _buf(uhat_in)
+    po, do, _k2 = _buf(duhat_out, writable=True)
+    if di != do:
+        raise ValueError("input and output must both be host or both be device buffers")
+    _check(load().dns_rhs(h, pi, po, di), "dns_rhs")
+
+
+def dns_step(h: int, n: int) -> None:
+    _check(load().dns_step(h, int(n)), "dns_step")
+
+
+def dns_step_profiled(h: int, n: int):
+    """(per-pass device ms [5], total device ms) for n plain-launched steps."""
+    arr = (ctypes.c_double * 5)()
+    tot = ctypes.c_double()
+    _check(load().dns_step_profiled(h, int(n), arr, ctypes.byref(tot)), "dns_step_profiled")
+    return list(arr), tot.value
+
+
+def dns_synchronize(h: int) -> None:
+    _check(load().dns_synchronize(h), "dns_synchronize")
+
+
+def dns_energy(h: int) -> float:
+    v = ctypes.c_double()
+    _check(load().dns_energy(h, ctypes.byref(v)), "dns_energy")
+    return v.value
+
+
+def dns_dissipation(h: int) -> float:
+    v = ctypes.c_double()
+    _check(load().dns_dissipation(h, ctypes.byref(v)), "dns_dissipation")
+    return v.value
+
+
+def dns_spectrum(h: int, nshells: int) -> np.ndarray:
+    out = np.zeros(int(nshells))
+    _check(load().dns_spectrum(h, out.ctypes.data_as(_dp), int(nshells)), "dns_spectrum")
+    return out
+
+
+def dns_time(h: int):
+    t, s = ctypes.c_double(), ctypes.c_long()
+    _check(load().dns_time(h, ctypes.byref(t), ctypes.byref(s)), "dns_time")
+    return t.value, s.value
+
+
+def dns_set_time(h: int, t: float, step: int) -> None:
+    _check(load().dns_set_time(h, float(t), int(step)), "dns_set_time")
+
+
+def dns_query(h: int) -> dict:
+    N, dt_, km = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    nu, dt = ctypes.c_double(), ctypes.c_double()
+    _check(load().dns_query(h, ctypes.byref(N), ctypes.byref(dt_), ctypes.byref(km), ctypes.byref(nu),
+                            ctypes.byref(dt)), "dns_query")
+    return {"N": N.value, "dtype": dt_.value, "kmax": km.value, "nu": nu.value, "dt": dt.value}
+
+
+def dns_device_bytes(h: int) -> int:
+    b = ctypes.c_longlong()
+    _check(load().dns_device_bytes(h, ctypes.byref(b)), "dns_device_bytes")
+    return b.value
+
+
+def dns_strerror(status: int) -> str:
+    return load().dns_strerror(int(status)).decode()
+
+
+# ---------------------------------------------------------------- convenience
+def io_complex_dtype(dtype: int):
+    return np.complex64 if dtype == DNS_F32 else np.complex128
+
+
+class Solver:
+    """Owns one handle; methods forward to the entry points above."""
+
+    def __init__(self, N: int, nu: float, dt: float, dtype: int = DNS_F32, stream: int | None = None):
+        self.N, self.nu, self.dt, self.dtype = int(N), float(nu), float(dt), int(dtype)
+        self.h = dns_init(N, nu, dt, dtype, stream)
+
+    def close(self):
+        if self.h:
+            dns_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def spectral_shape(self):
+        return (3, self.N, self.N, self.N // 2 + 1)
+
+    def set_velocity(self, uhat):
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=io_complex_dtype(self.dtype))
+        dns_set_velocity(self.h, uhat)
+
+    def set_velocity_physical(self, u):
+        if isinstance(u, np.ndarray):
+            u = np.ascontiguousarray(u, dtype=np.float32 if self.dtype == DNS_F32 else np.float64)
+        dns_set_velocity_physical(self.h, u)
+
+    def get_velocity(self, out=None):
+        if out is None:
+            out = np.empty(self.spectral_shape, io_complex_dtype(self.dtype))
+        dns_get_velocity(self.h, out)
+        return out
+
+    def rhs(self, uhat, out=None):
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=io_complex_dtype(self.dtype))
+            if out is None:
+                out = np.empty(self.spectral_shape, io_complex_dtype(self.dtype))
+        dns_rhs(self.h, uhat, out)
+        return out
+
+    def step(self, n: int = 1):
+        dns_step(self.h, n)
+
+    def synchronize(self):
+        dns_synchronize(self.h)
+
+    def energy(self) -> float:
+        return dns_energy(self.h)
+
+    def dissipation(self) -> float:
+        return dns_dissipation(self.h)
+
+    def spectrum(self, nshells: int | None = None) -> np.ndarray:
+        if nshells is None:
+            nshells = int(np.floor(np.sqrt(3.0) * self.N / 2 + 0.5)) + 1
+        return dns_spectrum(self.h, nshells)
+
+    def time(self):
+        return dns_time(self.h)
