@@ -34,12 +34,13 @@ SEED = 2024
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--N", type=int, default=512)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
+    p.add_argument("--no-ensemble", action="store_true")
     return p.parse_args()
 
 
@@ -123,23 +124,27 @@ def pass_bytes(N, dtype, stage):
     Kx, Kz = 2 * K + 1, K + 1
     cr = 16 if dtype == 1 else 8           # field complex bytes
     ca = 8 if dtype == 0 else 16           # accumulator complex bytes
-    S = 3 * Kx * Kx * Kz                   # state elements (3 components)
-    p1 = 3 * Kx * Kx * Kz * cr + 6 * N * Kx * Kz * cr
+    S = 3 * Kx * Kx * Kz                   # stored modes (3 components)
+    p1 = 2 * S * cr + 6 * N * Kx * Kz * cr               # u and omega^ in, 6 fields out
     p2 = 6 * N * Kx * Kz * cr + 6 * N * N * Kz * cr
     p3 = 6 * N * N * Kz * cr + 3 * N * N * Kz * cr
     p4 = 3 * N * N * Kz * cr + 3 * N * Kx * Kz * cr
+    p5a = 3 * N * Kx * Kz * cr + S * cr
     same = cr == ca
-    rd = 3 * N * Kx * Kz * cr + S * cr                 # N^ after y, stage input (viscous term)
+    rd = S * cr + S * cr                               # N^, stage input (viscous term)
     if stage < 3 and not (same and stage == 0):
         rd += S * ca                                   # u0
     if stage > 0:
         rd += S * ca                                   # u1
-    wr = 0
     if stage < 3:
-        wr += S * ca + S * cr                          # u1, next stage input
+        wr = S * ca + S * cr                           # u1, next stage input
     else:
-        wr += S * ca + (0 if same else S * cr)         # u0 (and the field copy)
-    return [p1, p2, p3, p4, rd + wr]
+        wr = S * ca + (0 if same else S * cr)          # u0 (and the field copy)
+    wr += S * cr                                       # omega^ of the next stage input
+    return [p1, p2, p3, p4, p5a, rd + wr]
+
+
+PASS_NAMES = ["p1_curl_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5a_xfwd", "p5b_update"]
 
 
 def survey_step_bytes(N, dtype):
@@ -202,8 +207,8 @@ def run_ours(args, rank, world, local_rank):
     peak, peak_src = measured_peaks()
     launches = 4 * args.steps
     per_stage = [pass_bytes(N, 0, st) for st in range(4)]
-    avg_bytes = [sum(p[i] for p in per_stage) / 4 for i in range(5)]
-    names = ["p1_curl_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5_xfwd_update"]
+    avg_bytes = [sum(p[i] for p in per_stage) / 4 for i in range(6)]
+    names = PASS_NAMES
     dom = int(np.argmax(pass_ms))
     dur = pass_ms[dom] / launches
     achieved = avg_bytes[dom] / (dur / 1e3) / 1e9
@@ -215,8 +220,9 @@ def run_ours(args, rank, world, local_rank):
                 "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
                 "step_bytes_216F_model": survey_step_bytes(N, 0),
                 "step_frac_216F_model": survey_step_bytes(N, 0) / (ms / args.steps / 1e3) / 1e9 / peak,
-                "pass_ms_per_launch": {names[i]: pass_ms[i] / launches for i in range(5)},
-                "pass_share": {names[i]: pass_ms[i] / max(prof_total, 1e-9) for i in range(5)}}
+                "pass_ms_per_launch": {names[i]: pass_ms[i] / launches for i in range(6)},
+                "pass_gbs": {names[i]: avg_bytes[i] / (pass_ms[i] / launches / 1e3) / 1e9 for i in range(6)},
+                "pass_share": {names[i]: pass_ms[i] / max(prof_total, 1e-9) for i in range(6)}}
 
     # ---- end to end through the C ABI with host buffers
     hin = torch.from_numpy(u32).pin_memory()
@@ -267,6 +273,8 @@ def run_ours(args, rank, world, local_rank):
         extra["fp32_energy_rel_err_vs_fp64"] = abs(E32 - Eref) / Eref
         extra["energy_steps"] = steps_done
     del uh
+    if not args.no_ensemble:
+        extra["ensemble"] = ensemble_bench(args, stream)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -276,9 +284,42 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded random-phase isotropic field)", "config": cfg,
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "gpu_launches": 20 * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "gpu_launches": 24 * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "energy": {"initial": E0, "after_steps": E32}, **extra}
     return line
+
+
+def ensemble_bench(args, stream):
+    """The batched ensemble (64 boxes at 64^3 + 16 at 96^3, FP32, dt = 0.005,
+    per-box k0 ~ U[2,6] and nu ~ U[0.005, 0.02]) timed over K graph-replayed
+    RK4 steps of all boxes."""
+    import torch
+    from paper_1607_00850_gb300 import dns, inputs
+    params = inputs.ensemble_params(64, 16)
+    Ns = [p[0] for p in params]
+    e = dns.Ensemble(Ns, [p[2] for p in params], 0.005, dns.DNS_F32, stream=stream.cuda_stream)
+    for b, (Nb, k0, nub, seed) in enumerate(params):
+        e.set_velocity(b, inputs.random_isotropic(Nb, seed=seed, k0=k0).astype(np.complex64))
+    e.step(args.warmup)
+    e.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    e.step(args.steps)
+    b.record(stream)
+    b.synchronize()
+    ms = a.elapsed_time(b)
+    E = e.energy()
+    e.close()
+    pts = float(sum(n ** 3 for n in Ns))
+    step_bytes = sum(sum(sum(pass_bytes(n, 0, st)) for st in range(4)) for n in Ns)
+    peak, src = measured_peaks()
+    return {"workload": "64 boxes at 64^3 + 16 boxes at 96^3, FP32, dt=0.005, 2/3 dealiasing, RK4",
+            "value": pts * args.steps / (ms / 1e3), "unit": "grid-point-steps/s",
+            "ms_per_step": ms / args.steps, "steps": args.steps,
+            "step_bytes_pruned": step_bytes,
+            "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
+            "step_frac_216F_model": sum(survey_step_bytes(n, 0) for n in Ns) / (ms / args.steps / 1e3) / 1e9 / peak,
+            "peak_source": src, "energy_min": float(E.min()), "energy_max": float(E.max())}
 
 
 def cpu_baseline(N, nu):

@@ -96,10 +96,10 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device);
 int dns_step(dns_handle h, int n);
 
 /* Advance n steps with plain kernel launches and CUDA events around every
- * launch, and add the device time of each pass to pass_ms[0..4]:
+ * launch, and add the device time of each pass to pass_ms[0..5]:
  * [0] inverse x transform + curl, [1] inverse y transform,
  * [2] z transforms + cross product, [3] forward y transform,
- * [4] forward x transform + dealias + projection + viscous term + RK4.
+ * [4] forward x transform (dealiased), [5] projection + viscous term + RK4.
  * total_ms receives the device time from the first launch to the last.
  * Synchronises the handle's stream. */
 int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms);
@@ -127,6 +127,29 @@ int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *d
 
 /* Bytes of device memory the handle holds. */
 int dns_device_bytes(dns_handle h, long long *bytes);
+
+/* ------------------------------------------------------------------------
+ * Batched ensemble: many independent boxes (each its own N, nu and initial
+ * field; one dt and dtype) advanced together.  Boxes of one N share every
+ * kernel launch (the grid covers all of them), and one RK4 step of every box
+ * is a single CUDA graph.  Same layouts, types and conventions as above, per
+ * box.  N as in dns_init; nbox >= 1; nu[b] > 0.
+ * ------------------------------------------------------------------------ */
+typedef struct dns_ens_ctx *dns_ensemble;
+
+int dns_ensemble_init(int nbox, const int *N, const double *nu, double dt, int dtype, void *cuda_stream,
+                      dns_ensemble *out);
+int dns_ensemble_free(dns_ensemble e);
+/* Set / read box b (0 <= b < nbox); synchronising like the single-box calls. */
+int dns_ensemble_set_velocity(dns_ensemble e, int box, const void *uhat, int on_device);
+int dns_ensemble_get_velocity(dns_ensemble e, int box, void *uhat, int on_device);
+/* Advance every box n RK4 steps (asynchronous graph replays). */
+int dns_ensemble_step(dns_ensemble e, int n);
+int dns_ensemble_synchronize(dns_ensemble e);
+/* Kinetic energy of every box, E[0..nbox-1] (double accumulation).  Returns
+ * DNS_ERR_NONFINITE if any is not finite. */
+int dns_ensemble_energy(dns_ensemble e, double *E);
+int dns_ensemble_time(dns_ensemble e, double *t, long *step);
 
 /* Human-readable name of a status code (static storage). */
 const char *dns_strerror(int status);

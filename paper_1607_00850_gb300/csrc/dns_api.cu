@@ -1,6 +1,6 @@
 // C-ABI of the single-GPU pseudo-spectral solver (include/dns.h).
 //
-// One RK4 step = 4 stages x 5 passes (dns_passes.cuh).  The step is captured
+// One RK4 step = 4 stages x 6 passes (dns_passes.cuh).  The step is captured
 // once into a CUDA graph and replayed.  All buffers are allocated at
 // dns_init; nothing is allocated on the stepping path.
 #include "dns.h"
@@ -46,7 +46,9 @@ struct dns_ctx {
     size_t creal = 0, cacc = 0, cio = 0;  // bytes per complex element
     void *U = nullptr, *U0 = nullptr, *U1 = nullptr, *A = nullptr, *B = nullptr;
     void *io = nullptr, *rin = nullptr, *rout = nullptr, *tw = nullptr;
+    void *Om = nullptr, *rom = nullptr;  // curl of the stage input (state boxes / rhs input)
     double *partials = nullptr, *sums = nullptr, *Ek = nullptr;
+    double *nu_box = nullptr;  // per-box viscosity when several boxes share the context
     int nblk = 0, smax = 0;
     double *host = nullptr;  // pinned read-back area
     cudaGraph_t graph = nullptr;
@@ -65,6 +67,8 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
         }                                     \
     } while (0)
 
+#define DNS_NPASS 6
+
 static const double RK_A[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 static const double RK_B[3] = {0.5, 0.5, 1.0};
 
@@ -72,7 +76,8 @@ static void release(dns_ctx *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    void *bufs[] = {h->U, h->U0, h->U1, h->A, h->B, h->io, h->rin, h->rout, h->tw, h->partials, h->sums, h->Ek};
+    void *bufs[] = {h->U, h->U0, h->U1, h->A, h->B, h->io, h->rin, h->rout, h->tw, h->partials, h->sums, h->Ek,
+                    h->nu_box, h->Om, h->rom};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->host) cudaFreeHost(h->host);
@@ -143,10 +148,10 @@ static cudaError_t acc_to_full(dns_ctx *h, const void *cmp, void *full) {
 }
 
 // --------------------------------------------------------------- the path
-static cudaError_t launch_front(dns_ctx *h, const void *Uin) {
+static cudaError_t launch_front(dns_ctx *h, const void *Uin, const void *Omin) {
     cudaError_t e;
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
-    if ((e = h->ps.p1(h->g, h->tw, Uin, h->A, scale, h->stream)) != cudaSuccess) return e;
+    if ((e = h->ps.p1(h->g, h->tw, Uin, Omin, h->A, scale, h->stream)) != cudaSuccess) return e;
     if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
     if ((e = h->ps.p3(h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
     return h->ps.p4(h->g, h->tw, h->B, h->A, h->stream);
@@ -160,7 +165,9 @@ static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
     a.Uout = (s < 3 || !h->same_type) ? h->U : nullptr;
     a.U0out = (s == 3) ? h->U0 : nullptr;
     a.dU = nullptr;
+    a.Om = h->Om;
     a.nu = h->nu;
+    a.nu_box = h->nu_box;
     a.adt = RK_A[s] * h->dt;
     a.bdt = s < 3 ? RK_B[s] * h->dt : 0.0;
     a.stage = s;
@@ -178,7 +185,7 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
     for (int s = 0; s < 4; ++s) {
         dns::UpdateArgsErased a = stage_args(h, s);
-        if ((e = h->ps.p1(h->g, h->tw, a.U, h->A, scale, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p1(h->g, h->tw, a.U, h->Om, h->A, scale, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
         if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
@@ -186,42 +193,85 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
         if ((e = mark()) != cudaSuccess) return e;
         if ((e = h->ps.p4(h->g, h->tw, h->B, h->A, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p5(h->g, h->tw, h->A, a, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = h->ps.p5b(h->g, h->B, a, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
-// --------------------------------------------------------------- API
-extern "C" {
-
-const char *dns_strerror(int status) {
-    switch (status) {
-        case DNS_OK: return "ok";
-        case DNS_ERR_ARG: return "invalid argument";
-        case DNS_ERR_OOM: return "out of memory";
-        case DNS_ERR_CUDA: return "CUDA error";
-        case DNS_ERR_TIMEOUT: return "bounded device wait timed out";
-        case DNS_ERR_NONFINITE: return "non-finite value in the state";
-        case DNS_ERR_UNSUPPORTED: return "unsupported size, dtype or option";
-        default: return "unknown status";
-    }
+// --------------------------------------------------------------- per-box state I/O
+static inline void *box_ptr(void *base, long long elems, size_t eb, int b) {
+    return (char *)base + (size_t)b * (size_t)elems * eb;
 }
 
-const char *dns_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
+// omega^ of box b's stage input (the next P1 reads it)
+static cudaError_t curl_box(dns_ctx *h, int b) {
+    Geo g1 = h->g;
+    g1.nb = 1;
+    return h->ps.curl(g1, box_ptr(h->U, h->g.bS, h->creal, b), box_ptr(h->Om, h->g.bS, h->creal, b), h->stream);
+}
 
-int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_handle *out) {
-    if (!out) return DNS_ERR_ARG;
-    *out = nullptr;
-    if (dtype < DNS_F32 || dtype > DNS_F32_ACC64) return DNS_ERR_ARG;
-    if (!(nu > 0.0) || !(dt > 0.0) || !std::isfinite(nu) || !std::isfinite(dt)) return DNS_ERR_ARG;
+// full-layout field (host or device) -> box b's stage input and step-start state
+static int set_state(dns_ctx *h, int b, const void *uhat, int on_device) {
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    const void *src = uhat;
+    if (!on_device) {
+        CK(cudaMemcpyAsync(h->io, uhat, bytes, cudaMemcpyHostToDevice, h->stream));
+        src = h->io;
+    }
+    CK(full_to_state(h, src, box_ptr(h->U, h->g.bS, h->creal, b), box_ptr(h->U0, h->g.bS, h->cacc, b)));
+    CK(curl_box(h, b));
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+static int get_state(dns_ctx *h, int b, void *uhat, int on_device) {
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    const void *u0 = box_ptr(h->U0, h->g.bS, h->cacc, b);
+    if (on_device) {
+        CK(acc_to_full(h, u0, uhat));
+    } else {
+        CK(acc_to_full(h, u0, h->io));
+        CK(cudaMemcpyAsync(uhat, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return DNS_OK;
+}
+
+static int stats_sums_box(dns_ctx *h, int b, double *se, double *sd) {
+    const void *u0 = box_ptr(h->U0, h->g.bS, h->cacc, b);
+    if (h->dtype == DNS_F32)
+        dns::k_energy_partials<float><<<h->nblk, 256, 0, h->stream>>>(h->g, (const float2 *)u0, h->partials);
+    else
+        dns::k_energy_partials<double><<<h->nblk, 256, 0, h->stream>>>(h->g, (const double2 *)u0, h->partials);
+    CK(cudaGetLastError());
+    dns::k_sum_partials<<<1, 32, 0, h->stream>>>(h->partials, h->nblk, 2, h->sums);
+    CK(cudaGetLastError());
+    CK(cudaMemcpyAsync(h->host, h->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    *se = h->host[0];
+    *sd = h->host[1];
+    return DNS_OK;
+}
+
+// --------------------------------------------------------------- handles
+// One context holds nb boxes of one mesh size: every pass covers all of
+// them in one launch.  nu_host[b] is box b's viscosity.
+static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype, cudaStream_t stream,
+                      dns_ctx **out) {
+    if (dtype < DNS_F32 || dtype > DNS_F32_ACC64 || nb < 1 || !nu_host) return DNS_ERR_ARG;
+    if (!(dt > 0.0) || !std::isfinite(dt)) return DNS_ERR_ARG;
+    for (int b = 0; b < nb; ++b)
+        if (!(nu_host[b] > 0.0) || !std::isfinite(nu_host[b])) return DNS_ERR_ARG;
     dns::PassGetter get = dns::getter_for(N);
     if (!get) return DNS_ERR_UNSUPPORTED;
     dns_ctx *h = new (std::nothrow) dns_ctx();
     if (!h) return DNS_ERR_OOM;
     h->N = N;
     h->dtype = dtype;
-    h->nu = nu;
+    h->nu = nu_host[0];
     h->dt = dt;
     if (!get(dtype, &h->ps)) {
         delete h;
@@ -237,6 +287,10 @@ int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_hand
     g.sS = (long long)g.Kx * g.Kx * g.Kzp;
     g.sA = (long long)N * g.Kx * g.Kzp;
     g.sB = (long long)N * N * g.Kzp;
+    g.nb = nb;
+    g.bS = 3 * g.sS;
+    g.bA = 6 * g.sA;
+    g.bB = 6 * g.sB;
     h->creal = dtype == DNS_F64 ? 16 : 8;
     h->cacc = dtype == DNS_F32 ? 8 : 16;
     h->cio = h->cacc;
@@ -245,18 +299,21 @@ int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_hand
     const size_t nfull = 3ull * N * N * (N / 2 + 1);
     h->nblk = 2 * 152;
     h->smax = (int)std::floor(std::sqrt(3.0) * K + 0.5) + 1;
-    if (!rc) rc = dev_alloc(h, &h->U, 3 * g.sS * h->creal);
-    if (!rc) rc = dev_alloc(h, &h->U0, 3 * g.sS * h->cacc);
-    if (!rc) rc = dev_alloc(h, &h->U1, 3 * g.sS * h->cacc);
-    if (!rc) rc = dev_alloc(h, &h->A, 6 * g.sA * h->creal);
-    if (!rc) rc = dev_alloc(h, &h->B, 6 * g.sB * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->U, nb * 3 * g.sS * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->U0, nb * 3 * g.sS * h->cacc);
+    if (!rc) rc = dev_alloc(h, &h->U1, nb * 3 * g.sS * h->cacc);
+    if (!rc) rc = dev_alloc(h, &h->A, nb * 6 * g.sA * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->B, nb * 6 * g.sB * h->creal);
     if (!rc) rc = dev_alloc(h, &h->io, nfull * h->cio);
     if (!rc) rc = dev_alloc(h, &h->rin, 3 * g.sS * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->Om, nb * 3 * g.sS * h->creal);
+    if (!rc) rc = dev_alloc(h, &h->rom, 3 * g.sS * h->creal);
     if (!rc) rc = dev_alloc(h, &h->rout, 3 * g.sS * h->cacc);
     if (!rc) rc = dev_alloc(h, &h->tw, (size_t)N * h->creal);
     if (!rc) rc = dev_alloc(h, (void **)&h->partials, sizeof(double) * 2 * h->nblk);
     if (!rc) rc = dev_alloc(h, (void **)&h->sums, sizeof(double) * 2);
     if (!rc) rc = dev_alloc(h, (void **)&h->Ek, sizeof(double) * h->smax);
+    if (!rc && nb > 1) rc = dev_alloc(h, (void **)&h->nu_box, sizeof(double) * nb);
     if (!rc && cudaMallocHost((void **)&h->host, sizeof(double) * (4 + h->smax)) != cudaSuccess) {
         h->host = nullptr;
         rc = DNS_ERR_OOM;
@@ -265,8 +322,8 @@ int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_hand
         release(h);
         return rc;
     }
-    if (cuda_stream) {
-        h->stream = (cudaStream_t)cuda_stream;
+    if (stream) {
+        h->stream = stream;
     } else {
         if (cudaStreamCreate(&h->stream) != cudaSuccess) {
             h->stream = nullptr;
@@ -290,9 +347,12 @@ int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_hand
     } else {
         e = cudaMemcpy(h->tw, twd.data(), twd.size() * sizeof(double), cudaMemcpyHostToDevice);
     }
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, 3 * g.sS * h->creal, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, 3 * g.sS * h->cacc, h->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, 3 * g.sS * h->cacc, h->stream);
+    if (e == cudaSuccess && nb > 1)
+        e = cudaMemcpy(h->nu_box, nu_host, sizeof(double) * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, nb * 3 * g.sS * h->creal, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, nb * 3 * g.sS * h->cacc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, nb * 3 * g.sS * h->cacc, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->Om, 0, nb * 3 * g.sS * h->creal, h->stream);
     if (e == cudaSuccess) e = h->ps.prepare();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -302,6 +362,30 @@ int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_hand
     }
     *out = h;
     return DNS_OK;
+}
+
+// --------------------------------------------------------------- API
+extern "C" {
+
+const char *dns_strerror(int status) {
+    switch (status) {
+        case DNS_OK: return "ok";
+        case DNS_ERR_ARG: return "invalid argument";
+        case DNS_ERR_OOM: return "out of memory";
+        case DNS_ERR_CUDA: return "CUDA error";
+        case DNS_ERR_TIMEOUT: return "bounded device wait timed out";
+        case DNS_ERR_NONFINITE: return "non-finite value in the state";
+        case DNS_ERR_UNSUPPORTED: return "unsupported size, dtype or option";
+        default: return "unknown status";
+    }
+}
+
+const char *dns_last_cuda_error(void) { return cudaGetErrorString(g_last_cuda); }
+
+int dns_init(int N, double nu, double dt, int dtype, void *cuda_stream, dns_handle *out) {
+    if (!out) return DNS_ERR_ARG;
+    *out = nullptr;
+    return ctx_create(N, 1, &nu, dt, dtype, (cudaStream_t)cuda_stream, out);
 }
 
 int dns_free(dns_handle h) {
@@ -319,15 +403,7 @@ int dns_synchronize(dns_handle h) {
 
 int dns_set_velocity(dns_handle h, const void *uhat, int on_device) {
     if (!h || !uhat) return DNS_ERR_ARG;
-    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
-    const void *src = uhat;
-    if (!on_device) {
-        CK(cudaMemcpyAsync(h->io, uhat, bytes, cudaMemcpyHostToDevice, h->stream));
-        src = h->io;
-    }
-    CK(full_to_state(h, src, h->U, h->U0));
-    CK(cudaStreamSynchronize(h->stream));
-    return DNS_OK;
+    return set_state(h, 0, uhat, on_device);
 }
 
 int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
@@ -344,7 +420,8 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
     dns::UpdateArgsErased a{};
     a.dU = h->rout;
     a.stage = -2;
-    CK(h->ps.p5(h->g, h->tw, h->A, a, h->stream));
+    CK(h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream));
+    CK(h->ps.p5b(h->g, h->B, a, h->stream));
     const long long n = 3 * h->g.sS;
     CK(cudaMemcpyAsync(h->U0, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
     if (h->same_type) {
@@ -353,21 +430,14 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
         k_convert<double2, float2><<<grid_for(n), 256, 0, h->stream>>>((const double2 *)h->rout, (float2 *)h->U, n);
         CK(cudaGetLastError());
     }
+    CK(curl_box(h, 0));
     CK(cudaStreamSynchronize(h->stream));
     return DNS_OK;
 }
 
 int dns_get_velocity(dns_handle h, void *uhat, int on_device) {
     if (!h || !uhat) return DNS_ERR_ARG;
-    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
-    if (on_device) {
-        CK(acc_to_full(h, h->U0, uhat));
-    } else {
-        CK(acc_to_full(h, h->U0, h->io));
-        CK(cudaMemcpyAsync(uhat, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
-    }
-    CK(cudaStreamSynchronize(h->stream));
-    return DNS_OK;
+    return get_state(h, 0, uhat, on_device);
 }
 
 int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
@@ -379,13 +449,17 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
         src = h->io;
     }
     CK(full_to_state(h, src, h->rin, nullptr));
-    CK(launch_front(h, h->rin));
+    Geo g1 = h->g;
+    g1.nb = 1;
+    CK(h->ps.curl(g1, h->rin, h->rom, h->stream));
+    CK(launch_front(h, h->rin, h->rom));
     dns::UpdateArgsErased a{};
     a.U = h->rin;
     a.dU = h->rout;
     a.nu = h->nu;
     a.stage = -1;
-    CK(h->ps.p5(h->g, h->tw, h->A, a, h->stream));
+    CK(h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream));
+    CK(h->ps.p5b(h->g, h->B, a, h->stream));
     if (on_device) {
         CK(acc_to_full(h, h->rout, duhat_out));
     } else {
@@ -428,10 +502,10 @@ int dns_step(dns_handle h, int n) {
 
 int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms) {
     if (!h || n < 0 || !pass_ms) return DNS_ERR_ARG;
-    for (int i = 0; i < 5; ++i) pass_ms[i] = 0.0;
+    for (int i = 0; i < DNS_NPASS; ++i) pass_ms[i] = 0.0;
     if (total_ms) *total_ms = 0.0;
     if (n == 0) return DNS_OK;
-    const int per = 20;
+    const int per = 4 * DNS_NPASS;
     std::vector<cudaEvent_t> ev((size_t)per * n + 1, nullptr);
     int rc = DNS_OK;
     for (auto &x : ev)
@@ -452,7 +526,7 @@ int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms) {
         for (size_t i = 0; i + 1 < ev.size(); ++i) {
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
-            pass_ms[i % 5] += ms;
+            pass_ms[i % DNS_NPASS] += ms;
         }
         float tot = 0.f;
         cudaEventElapsedTime(&tot, ev[0], ev.back());
@@ -465,20 +539,7 @@ int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms) {
     return rc;
 }
 
-static int stats_sums(dns_handle h, double *se, double *sd) {
-    if (h->dtype == DNS_F32)
-        dns::k_energy_partials<float><<<h->nblk, 256, 0, h->stream>>>(h->g, (const float2 *)h->U0, h->partials);
-    else
-        dns::k_energy_partials<double><<<h->nblk, 256, 0, h->stream>>>(h->g, (const double2 *)h->U0, h->partials);
-    CK(cudaGetLastError());
-    dns::k_sum_partials<<<1, 32, 0, h->stream>>>(h->partials, h->nblk, 2, h->sums);
-    CK(cudaGetLastError());
-    CK(cudaMemcpyAsync(h->host, h->sums, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
-    CK(cudaStreamSynchronize(h->stream));
-    *se = h->host[0];
-    *sd = h->host[1];
-    return DNS_OK;
-}
+static int stats_sums(dns_handle h, double *se, double *sd) { return stats_sums_box(h, 0, se, sd); }
 
 int dns_energy(dns_handle h, double *E) {
     if (!h || !E) return DNS_ERR_ARG;
@@ -540,6 +601,164 @@ int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *d
 int dns_device_bytes(dns_handle h, long long *bytes) {
     if (!h || !bytes) return DNS_ERR_ARG;
     *bytes = h->bytes;
+    return DNS_OK;
+}
+
+// --------------------------------------------------------------- ensemble
+}  // extern "C"
+
+struct dns_ens_ctx {
+    int nbox = 0, dtype = 0;
+    double dt = 0, t = 0;
+    long step = 0;
+    std::vector<dns_ctx *> cls;    // one context per distinct N
+    std::vector<int> box_cls, box_idx;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+static void ens_release(dns_ens_ctx *e) {
+    if (!e) return;
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    for (dns_ctx *c : e->cls) release(c);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+extern "C" {
+
+int dns_ensemble_init(int nbox, const int *N, const double *nu, double dt, int dtype, void *cuda_stream,
+                      dns_ensemble *out) {
+    if (!out) return DNS_ERR_ARG;
+    *out = nullptr;
+    if (nbox < 1 || !N || !nu) return DNS_ERR_ARG;
+    if (dtype < DNS_F32 || dtype > DNS_F32_ACC64 || !(dt > 0.0) || !std::isfinite(dt)) return DNS_ERR_ARG;
+    for (int b = 0; b < nbox; ++b) {
+        if (!dns::getter_for(N[b])) return DNS_ERR_UNSUPPORTED;
+        if (!(nu[b] > 0.0) || !std::isfinite(nu[b])) return DNS_ERR_ARG;
+    }
+    dns_ens_ctx *e = new (std::nothrow) dns_ens_ctx();
+    if (!e) return DNS_ERR_OOM;
+    e->nbox = nbox;
+    e->dtype = dtype;
+    e->dt = dt;
+    if (cuda_stream) {
+        e->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreate(&e->stream) != cudaSuccess) {
+            delete e;
+            return DNS_ERR_CUDA;
+        }
+        e->own_stream = true;
+    }
+    // group boxes by mesh size, in order of first appearance
+    std::vector<int> sizes;
+    e->box_cls.resize(nbox);
+    e->box_idx.resize(nbox);
+    std::vector<std::vector<double>> nus;
+    for (int b = 0; b < nbox; ++b) {
+        int c = -1;
+        for (size_t i = 0; i < sizes.size(); ++i)
+            if (sizes[i] == N[b]) c = (int)i;
+        if (c < 0) {
+            c = (int)sizes.size();
+            sizes.push_back(N[b]);
+            nus.emplace_back();
+        }
+        e->box_cls[b] = c;
+        e->box_idx[b] = (int)nus[c].size();
+        nus[c].push_back(nu[b]);
+    }
+    for (size_t c = 0; c < sizes.size(); ++c) {
+        dns_ctx *h = nullptr;
+        int rc = ctx_create(sizes[c], (int)nus[c].size(), nus[c].data(), dt, dtype, e->stream, &h);
+        if (rc) {
+            ens_release(e);
+            return rc;
+        }
+        e->cls.push_back(h);
+    }
+    *out = e;
+    return DNS_OK;
+}
+
+int dns_ensemble_free(dns_ensemble e) {
+    if (!e) return DNS_OK;
+    cudaStreamSynchronize(e->stream);
+    ens_release(e);
+    return DNS_OK;
+}
+
+int dns_ensemble_set_velocity(dns_ensemble e, int box, const void *uhat, int on_device) {
+    if (!e || !uhat || box < 0 || box >= e->nbox) return DNS_ERR_ARG;
+    return set_state(e->cls[e->box_cls[box]], e->box_idx[box], uhat, on_device);
+}
+
+int dns_ensemble_get_velocity(dns_ensemble e, int box, void *uhat, int on_device) {
+    if (!e || !uhat || box < 0 || box >= e->nbox) return DNS_ERR_ARG;
+    return get_state(e->cls[e->box_cls[box]], e->box_idx[box], uhat, on_device);
+}
+
+int dns_ensemble_step(dns_ensemble e, int n) {
+    if (!e || n < 0) return DNS_ERR_ARG;
+    if (n == 0) return DNS_OK;
+    if (!e->exec) {
+        CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t err = cudaSuccess;
+        for (dns_ctx *h : e->cls)
+            if (err == cudaSuccess) err = enqueue_step(h, nullptr);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e2 = cudaStreamEndCapture(e->stream, &graph);
+        if (err != cudaSuccess || e2 != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            g_last_cuda = err != cudaSuccess ? err : e2;
+            cudaGetLastError();
+            return DNS_ERR_CUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        err = cudaGraphInstantiate(&exec, graph, 0);
+        if (err != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            g_last_cuda = err;
+            return DNS_ERR_CUDA;
+        }
+        e->graph = graph;
+        e->exec = exec;
+    }
+    for (int i = 0; i < n; ++i) CK(cudaGraphLaunch(e->exec, e->stream));
+    e->t += n * e->dt;
+    e->step += n;
+    return DNS_OK;
+}
+
+int dns_ensemble_synchronize(dns_ensemble e) {
+    if (!e) return DNS_ERR_ARG;
+    CK(cudaStreamSynchronize(e->stream));
+    return DNS_OK;
+}
+
+int dns_ensemble_energy(dns_ensemble e, double *E) {
+    if (!e || !E) return DNS_ERR_ARG;
+    int status = DNS_OK;
+    for (int b = 0; b < e->nbox; ++b) {
+        dns_ctx *h = e->cls[e->box_cls[b]];
+        double se, sd;
+        int rc = stats_sums_box(h, e->box_idx[b], &se, &sd);
+        if (rc) return rc;
+        const double N3 = (double)h->N * h->N * h->N;
+        E[b] = se / (2.0 * N3 * N3);
+        if (!std::isfinite(E[b])) status = DNS_ERR_NONFINITE;
+    }
+    return status;
+}
+
+int dns_ensemble_time(dns_ensemble e, double *t, long *step) {
+    if (!e) return DNS_ERR_ARG;
+    if (t) *t = e->t;
+    if (step) *step = e->step;
     return DNS_OK;
 }
 

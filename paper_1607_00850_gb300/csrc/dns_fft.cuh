@@ -56,43 +56,71 @@ template <int SIGN, typename T> __device__ __forceinline__ T cmul_si(T a) {
 template <typename T, typename S> __device__ __forceinline__ T cscale(T a, S s) { a.x *= s; a.y *= s; return a; }
 
 // ---------------------------------------------------------------------------
-// Radix plan: N = 3^b * 2^a (b <= 1).  Radix 3 first, then radix 8 stages,
-// then a 4 or 4*4 (or a lone 2) for the remaining power of two.
+// Radix plan: N = 3^b * 2^a (b <= 1).  A radix-3 stage first, then the power
+// of two split into the fewest stages whose radices are at most MAXR (8, 16
+// or 32), as equal as possible, smaller first: 2^9 with MAXR 8 -> 8*8*8,
+// with 32 -> 16*32;
+// 2^10 with 8 -> 4*4*8*8.
 struct FftPlan {
     int nst;
     int r[8];
     int ns[8];  // product of the radices of the earlier stages
 };
 
-__host__ __device__ constexpr FftPlan make_plan(int N) {
+__host__ __device__ constexpr FftPlan make_plan(int N, int MAXR = 8) {
     FftPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
     int n = N;
     if (n % 3 == 0) { p.r[p.nst++] = 3; n /= 3; }
     int a = 0;
     while ((1 << a) < n) ++a;
-    int q = a / 3, rem = a % 3;
-    if (rem == 1 && q == 0) {
-        p.r[p.nst++] = 2;
-    } else {
-        int n8 = (rem == 1) ? q - 1 : q;
-        for (int i = 0; i < n8; ++i) p.r[p.nst++] = 8;
-        if (rem == 1) { p.r[p.nst++] = 4; p.r[p.nst++] = 4; }
-        if (rem == 2) p.r[p.nst++] = 4;
+    int lmax = MAXR >= 32 ? 5 : (MAXR >= 16 ? 4 : 3);
+    int ns_ = (a + lmax - 1) / lmax;  // number of power-of-two stages
+    for (int s = 0; s < ns_; ++s) {  // smaller radices first
+        int e = a / ns_ + (s >= ns_ - a % ns_ ? 1 : 0);
+        p.r[p.nst++] = 1 << e;
     }
     int ns = 1;
     for (int s = 0; s < p.nst; ++s) { p.ns[s] = ns; ns *= p.r[s]; }
     return p;
 }
 
-__host__ __device__ constexpr int plan_max_radix(int N) {
-    FftPlan p = make_plan(N);
+__host__ __device__ constexpr int plan_max_radix(int N, int MAXR = 8) {
+    FftPlan p = make_plan(N, MAXR);
     int m = 1;
     for (int s = 0; s < p.nst; ++s) m = p.r[s] > m ? p.r[s] : m;
     return m;
 }
 
+// cos(2 pi m / 32), m = 0..8 (first quadrant; the rest follow by symmetry)
+__host__ __device__ constexpr double kCos32(int m) {
+    return m == 0 ? 1.0
+         : m == 1 ? 0.980785280403230449126
+         : m == 2 ? 0.923879532511286756128
+         : m == 3 ? 0.831469612302545237079
+         : m == 4 ? 0.707106781186547524401
+         : m == 5 ? 0.555570233019602224743
+         : m == 6 ? 0.382683432365089771728
+         : m == 7 ? 0.195090322016128267848
+         : 0.0;
+}
+// exp(2 pi i m / 32) as (cos, sin), any m >= 0
+__host__ __device__ constexpr double w32_re(int m) {
+    return (m % 32) / 8 == 0 ? kCos32(m % 8)
+         : (m % 32) / 8 == 1 ? -kCos32(8 - m % 8)
+         : (m % 32) / 8 == 2 ? -kCos32(m % 8)
+         : kCos32(8 - m % 8);
+}
+__host__ __device__ constexpr double w32_im(int m) {
+    return (m % 32) / 8 == 0 ? kCos32(8 - m % 8)
+         : (m % 32) / 8 == 1 ? kCos32(m % 8)
+         : (m % 32) / 8 == 2 ? -kCos32(8 - m % 8)
+         : -kCos32(m % 8);
+}
+
 // ---------------------------------------------------------------------------
 // Small DFTs in registers: X[k] = sum_n v[n] exp(SIGN 2 pi i k n / R).
+template <int P, int Q, int SIGN, typename T> __device__ __forceinline__ void dft_pq(T *v);
+
 template <int R, int SIGN, typename T> __device__ __forceinline__ void dft(T *v) {
     typedef typename RealOf<T>::t real;
     if constexpr (R == 2) {
@@ -132,8 +160,58 @@ template <int R, int SIGN, typename T> __device__ __forceinline__ void dft(T *v)
         v[6] = csub(e[2], o2);
         v[3] = cadd(e[3], o3);
         v[7] = csub(e[3], o3);
+    } else if constexpr (R == 16) {
+        dft_pq<4, 4, SIGN>(v);
+    } else if constexpr (R == 32) {
+        dft_pq<8, 4, SIGN>(v);
     } else {
-        static_assert(R == 2 || R == 3 || R == 4 || R == 8, "unsupported radix");
+        static_assert(R == 2 || R == 3 || R == 4 || R == 8 || R == 16 || R == 32, "unsupported radix");
+    }
+}
+
+// Composite DFT of length P*Q in registers (Cooley-Tukey with n = Q n1 + n2,
+// k = k1 + P k2): P-point DFTs over n1, twiddles w_{PQ}^{n2 k1}, Q-point DFTs
+// over n2.  P*Q divides 32, so the twiddles are compile-time constants.
+template <int P, int Q, int SIGN, typename T> __device__ __forceinline__ void dft_pq(T *v) {
+    typedef typename RealOf<T>::t real;
+    constexpr int PQ = P * Q;
+    T y[Q][P];
+#pragma unroll
+    for (int n2 = 0; n2 < Q; ++n2) {
+        T t[P];
+#pragma unroll
+        for (int n1 = 0; n1 < P; ++n1) t[n1] = v[Q * n1 + n2];
+        dft<P, SIGN>(t);
+#pragma unroll
+        for (int k1 = 0; k1 < P; ++k1) y[n2][k1] = t[k1];
+    }
+#pragma unroll
+    for (int n2 = 1; n2 < Q; ++n2) {
+#pragma unroll
+        for (int k1 = 1; k1 < P; ++k1) {
+            const int m = ((n2 * k1) % PQ) * (32 / PQ);
+            if (m == 8) {
+                y[n2][k1] = cmul_si<SIGN>(y[n2][k1]);
+            } else if (m == 24) {
+                y[n2][k1] = cmul_si<-SIGN>(y[n2][k1]);
+            } else if (m == 16) {
+                y[n2][k1] = cscale(y[n2][k1], (real)-1);
+            } else if (m != 0) {
+                T w;
+                w.x = (real)w32_re(m);
+                w.y = (real)(SIGN * w32_im(m));
+                y[n2][k1] = cmul(y[n2][k1], w);
+            }
+        }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < P; ++k1) {
+        T t[Q];
+#pragma unroll
+        for (int n2 = 0; n2 < Q; ++n2) t[n2] = y[n2][k1];
+        dft<Q, SIGN>(t);
+#pragma unroll
+        for (int k2 = 0; k2 < Q; ++k2) v[k1 + P * k2] = t[k2];
     }
 }
 
@@ -141,13 +219,13 @@ template <int R, int SIGN, typename T> __device__ __forceinline__ void dft(T *v)
 // The engine.  tw[m] = exp(-2 pi i m / N) (forward table); SIGN = +1 uses
 // its conjugate.  Load(n, c) -> value of row n of line c for the first
 // stage; Store(n, c, v) consumes row n of line c after the last stage.
-template <typename real, int N, int W, int T, int SIGN, int S = 0>
+template <typename real, int N, int W, int T, int SIGN, int MAXR = 8, int S = 0>
 struct TileFFT {
     typedef typename CT<real>::t cplx;
     template <class Load, class Store>
     static __device__ __forceinline__ void run(cplx *tile, int ld, const cplx *tw, const Load &load,
                                                const Store &store) {
-        constexpr FftPlan P = make_plan(N);
+        constexpr FftPlan P = make_plan(N, MAXR);
         constexpr int R = P.r[S];
         constexpr int Ns = P.ns[S];
         constexpr int NB = N / R;
@@ -196,14 +274,84 @@ struct TileFFT {
             }
         }
         __syncthreads();
-        if constexpr (!last) TileFFT<real, N, W, T, SIGN, S + 1>::run(tile, ld, tw, load, store);
+        if constexpr (!last) TileFFT<real, N, W, T, SIGN, MAXR, S + 1>::run(tile, ld, tw, load, store);
     }
 };
 
-// Threads for a W-column tile so that each thread holds about QT butterflies
-// of the largest radix.
-__host__ __device__ constexpr int tile_threads(int N, int W, int QT) {
-    int t = (N * W / plan_max_radix(N) + QT - 1) / QT;
+// ---------------------------------------------------------------------------
+// Row-mapped variant for lines that are contiguous in memory: NV lines of
+// length N in shared memory as tile[v * ldr + n + n/16] (one pad element per
+// 16 keeps every stage's accesses free of bank conflicts, including the
+// stride-R writes of a first stage).  Work item (v, j) = butterfly j of line
+// v, consecutive threads on consecutive j, so a first stage reading straight
+// from HBM is coalesced along the line.
+__host__ __device__ constexpr int row_ld(int N) { return N + N / 16; }
+__device__ __forceinline__ int radd(int n) { return n + (n >> 4); }
+
+template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0>
+struct RowFFT {
+    typedef typename CT<real>::t cplx;
+    // Load(v, n): first-stage input; Store(v, n, x): last-stage output.
+    template <class Load, class Store>
+    static __device__ __forceinline__ void run(cplx *tile, const cplx *tw, const Load &load, const Store &store) {
+        constexpr FftPlan P = make_plan(N, MAXR);
+        constexpr int R = P.r[S];
+        constexpr int Ns = P.ns[S];
+        constexpr int NB = N / R;
+        constexpr int TOT = NB * NV;
+        constexpr int Q = (TOT + T - 1) / T;
+        constexpr bool first = (S == 0);
+        constexpr bool last = (S == P.nst - 1);
+        constexpr int TWS = N / (Ns * R);
+        constexpr int LDR = row_ld(N);
+        cplx v[Q][R];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int vl = idx / NB, j = idx % NB;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int n = j + r * NB;
+                    if constexpr (first) v[q][r] = load(vl, n);
+                    else v[q][r] = tile[vl * LDR + radd(n)];
+                }
+                if constexpr (!first) {
+                    const int k = j % Ns;
+#pragma unroll
+                    for (int r = 1; r < R; ++r) {
+                        cplx w = tw[r * k * TWS];
+                        if (SIGN > 0) w.y = -w.y;
+                        v[q][r] = cmul(v[q][r], w);
+                    }
+                }
+                dft<R, SIGN>(v[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int vl = idx / NB, j = idx % NB;
+                const int base = (j / Ns) * Ns * R + (j % Ns);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int n = base + r * Ns;
+                    if constexpr (last) store(vl, n, v[q][r]);
+                    else tile[vl * LDR + radd(n)] = v[q][r];
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (!last) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1>::run(tile, tw, load, store);
+    }
+};
+
+// Threads for a W-column tile so that no thread holds more than BUDGET
+// complex values in registers in any stage (BUDGET >= the largest radix).
+__host__ __device__ constexpr int tile_threads(int N, int W, int BUDGET) {
+    int t = (N * W + BUDGET - 1) / BUDGET;
     t = ((t + 31) / 32) * 32;
     return t < 32 ? 32 : (t > 1024 ? 1024 : t);
 }

@@ -1,14 +1,17 @@
 // The five passes of one evaluation of Eq. NSfinal, fused with their
 // pointwise work (Mortensen, Sec. 2):
 //
-//   P1  curl (omega^ = i k x uhat) + inverse transform along x, 6 fields
+//   P1  inverse transform along x of u and omega^ = i k x uhat, 6 fields
+//       (omega^ is written by the previous stage's update, or by k_curl)
 //   P2  inverse transform along y, 6 fields
 //   P3  inverse real transform along z of 6 fields, u x omega pointwise,
 //       forward real transform along z of 3 fields (physical values never
 //       leave shared memory)
 //   P4  forward transform along y, 3 fields
-//   P5  forward transform along x, then Leray projection, viscous term and
-//       the RK4 stage update (or the bare right-hand side)
+//   P5a forward transform along x, 3 fields, stored modes only
+//   P5b Leray projection, viscous term and the RK4 stage update (or the
+//       bare right-hand side), streaming over the stored modes; it also
+//       writes the curl of the next stage input
 //
 // The inverse runs x, y, z and the forward z, y, x, the reverse order as
 // Eq. ffteq requires.  Storage is pruned to the 2/3-rule set: with
@@ -20,7 +23,8 @@
 // Buffers (complex, interleaved):
 //   state  S[3][Kx][Ky][Kzp]   Kx = Ky = 2K+1, Kz = K+1, Kzp = Kz rounded up to 4
 //   A      [6][N][Ky][Kzp]     after P1 (x physical); P4 writes its 3 fields here
-//   B      [6][N][N][Kzp]      after P2 (x, y physical); P3 writes N^ into fields 0..2
+//   B      [6][N][N][Kzp]      after P2 (x, y physical); P3 writes N^ into fields 0..2;
+//                              P5a writes the transformed N^ here in the state layout
 #pragma once
 
 #include "dns_fft.cuh"
@@ -32,10 +36,12 @@ struct Geo {
     long long sS;  // elements per state field  = Kx*Kx*Kzp
     long long sA;  // elements per A field      = N*Kx*Kzp
     long long sB;  // elements per B field      = N*N*Kzp
+    int nb;        // boxes of this size advanced together (batch), >= 1
+    long long bS, bA, bB;  // elements between consecutive boxes in the state, A and B
 };
 
-// Arguments of P5.  stage in 0..3 performs that RK4 stage; stage = -1 writes
-// the right-hand side to dU instead.
+// Arguments of P5b.  stage in 0..3 performs that RK4 stage; stage = -1 writes
+// the right-hand side to dU instead; stage = -2 copies the transform to dU.
 template <typename real, typename acc>
 struct UpdateArgs {
     typedef typename CT<real>::t cplx;
@@ -46,7 +52,9 @@ struct UpdateArgs {
     cplx *Uout;      // next stage input (real type), nullptr when not needed
     cacc *U0out;     // after the last stage: the new step-start state
     cacc *dU;        // stage = -1: right-hand side out
+    cplx *Om;        // curl of the next stage input (stages 0..3), nullptr to skip
     double nu;
+    const double *nu_box;  // per-box viscosity (batched boxes), or nullptr for nu
     double adt;      // a_s * dt
     double bdt;      // b_s * dt
     int stage;
@@ -68,56 +76,72 @@ template <typename real> __device__ __forceinline__ void load_twiddles(typename 
 }
 
 // ------------------------------------------------------------------- P1
-template <typename real, int N, int W, int T>
-__global__ void __launch_bounds__(T) k_p1_curl_xinv(Geo g, const typename CT<real>::t *__restrict__ twg,
-                                                    const typename CT<real>::t *__restrict__ U,
-                                                    typename CT<real>::t *__restrict__ A, real scale) {
+// Inverse transform along x of u (fields 0..2, from U) and of omega^ = i k x
+// uhat (fields 3..5, from Om, written by the previous update or by k_curl).
+template <typename real, int N, int W, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p1_xinv(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                               const typename CT<real>::t *__restrict__ U,
+                                               const typename CT<real>::t *__restrict__ Om,
+                                               typename CT<real>::t *__restrict__ A, real scale) {
     typedef typename CT<real>::t cplx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     load_twiddles<real>(tw, twg, N);
     __syncthreads();
-    const int kz0 = blockIdx.x * W, jy = blockIdx.y, f = blockIdx.z;
+    const int box = blockIdx.x / 6, f = blockIdx.x % 6, kz0 = blockIdx.y * W, jy = blockIdx.z;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const real ky = (real)compact_to_k(jy, K);
-    const long long sS = g.sS;
+    const cplx *src = (f < 3 ? U + f * g.sS : Om + (f - 3) * g.sS) + box * g.bS + (long long)jy * Kzp;
+    cplx *dst = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         const int ix = row_to_compact<N>(n, K);
-        cplx z;
-        z.x = 0;
-        z.y = 0;
-        if (kz >= Kz || ix < 0) return z;
-        const long long m = ((long long)ix * Kx + jy) * Kzp + kz;
-        const real kx = (real)compact_to_k(ix, K), kzr = (real)kz;
-        cplx v;
-        if (f < 3) {
-            v = U[f * sS + m];
-        } else {
-            // omega^ = i k x uhat
-            cplx a, b;
-            real ka, kb;
-            if (f == 3) { a = U[2 * sS + m]; ka = ky; b = U[sS + m]; kb = kzr; }      // i(ky w - kz v)
-            else if (f == 4) { a = U[m]; ka = kzr; b = U[2 * sS + m]; kb = kx; }     // i(kz u - kx w)
-            else { a = U[sS + m]; ka = kx; b = U[m]; kb = ky; }                      // i(kx v - ky u)
-            const real re = ka * a.x - kb * b.x, im = ka * a.y - kb * b.y;
-            v.x = -im;
-            v.y = re;
-        }
-        v.x *= scale;
-        v.y *= scale;
-        return v;
+        if (kz >= Kz || ix < 0) return cmk<cplx>(0.0, 0.0);
+        const cplx v = src[(long long)ix * Kx * Kzp + kz];
+        return cmk<cplx>(v.x * scale, v.y * scale);
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
-        if (kz < Kz) A[f * g.sA + ((long long)n * Kx + jy) * Kzp + kz] = v;
+        if (kz < Kz) dst[(long long)n * Kx * Kzp + kz] = v;
     };
-    TileFFT<real, N, W, T, +1>::run(tile, W, tw, load, store);
+    TileFFT<real, N, W, T, +1, MAXR>::run(tile, W, tw, load, store);
+}
+
+// omega^ = i k x uhat on the stored modes (Eq. eqNS: omega = curl u):
+// (i(ky w - kz v), i(kz u - kx w), i(kx v - ky u)).
+template <typename cplx, typename real>
+__device__ __forceinline__ void curl_mode(real kx, real ky, real kz, cplx u, cplx v, cplx w, cplx &ox, cplx &oy,
+                                          cplx &oz) {
+    ox = cmk<cplx>(-(ky * w.y - kz * v.y), ky * w.x - kz * v.x);
+    oy = cmk<cplx>(-(kz * u.y - kx * w.y), kz * u.x - kx * w.x);
+    oz = cmk<cplx>(-(kx * v.y - ky * u.y), kx * v.x - ky * u.x);
+}
+
+template <typename real>
+__global__ void k_curl(Geo g, const typename CT<real>::t *__restrict__ U, typename CT<real>::t *__restrict__ Om) {
+    typedef typename CT<real>::t cplx;
+    const long long sS = g.sS;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= sS * g.nb) return;
+    const long long box = e / sS, mm = e % sS;
+    const int kz = (int)(mm % g.Kzp);
+    const long long r = mm / g.Kzp;
+    const int iy = (int)(r % g.Kx), ix = (int)(r / g.Kx);
+    const long long m = box * g.bS + mm;
+    if (kz >= g.Kz) {
+        Om[m] = Om[sS + m] = Om[2 * sS + m] = cmk<cplx>(0.0, 0.0);
+        return;
+    }
+    cplx ox, oy, oz;
+    curl_mode<cplx, real>((real)compact_to_k(ix, g.K), (real)compact_to_k(iy, g.K), (real)kz, U[m], U[sS + m],
+                          U[2 * sS + m], ox, oy, oz);
+    Om[m] = ox;
+    Om[sS + m] = oy;
+    Om[2 * sS + m] = oz;
 }
 
 // ------------------------------------------------------------------- P2
-template <typename real, int N, int W, int T>
+template <typename real, int N, int W, int T, int MAXR>
 __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                const typename CT<real>::t *__restrict__ A,
                                                typename CT<real>::t *__restrict__ B) {
@@ -127,10 +151,10 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
     cplx *tile = tw + N;
     load_twiddles<real>(tw, twg, N);
     __syncthreads();
-    const int kz0 = blockIdx.x * W, x = blockIdx.y, f = blockIdx.z;
+    const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 6, f = blockIdx.z % 6;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = A + f * g.sA + (long long)x * Kx * Kzp;
-    cplx *dst = B + f * g.sB + (long long)x * N * Kzp;
+    const cplx *src = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
+    cplx *dst = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         const int iy = row_to_compact<N>(n, K);
@@ -144,69 +168,100 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
         const int kz = kz0 + c;
         if (kz < Kz) dst[(long long)n * Kzp + kz] = v;
     };
-    TileFFT<real, N, W, T, +1>::run(tile, W, tw, load, store);
+    TileFFT<real, N, W, T, +1, MAXR>::run(tile, W, tw, load, store);
 }
 
 // ------------------------------------------------------------------- P3
-// L lines (consecutive y at one x) per block.  Pairs of real fields share
-// one complex transform: line p holds X_{2p} + i X_{2p+1}, extended to the
-// full length by Hermitian symmetry; after the inverse transform the real
-// and imaginary parts are the two physical fields.
-template <typename real, int N, int L, int T>
+// L lines (consecutive y at one x) per block, row-mapped (RowFFT).  Pairs of
+// real fields share one complex transform: virtual line (p, l) holds
+// X_{2p} + i X_{2p+1}, extended to the full length by Hermitian symmetry
+// (Z[n] = a + i b for n <= N/2, conj(a) + i conj(b) at n = N - kz); after
+// the inverse transform its real and imaginary parts are the two physical
+// fields.  The first inverse stage packs straight from HBM (coalesced along
+// kz); the cross product is computed inside the first forward stage, so the
+// physical values are read once from shared memory and never stored.
+template <typename real, int N, int L, int T, int MAXR>
 __global__ void __launch_bounds__(T) k_p3_z_cross(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                   typename CT<real>::t *__restrict__ B) {
     typedef typename CT<real>::t cplx;
-    constexpr int LD = 3 * L + 1;
+    constexpr int LDR = row_ld(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
-    cplx *tile = tw + N;
+    cplx *tile = tw + N;  // [3L][LDR]: pair p of line l at row p*L + l
     load_twiddles<real>(tw, twg, N);
-    const int K = g.K, Kz = g.Kz, Kzp = g.Kzp;
-    const long long line0 = (long long)blockIdx.x * L;  // = x*N + y0
+    __syncthreads();
+    const int K = g.K, Kzp = g.Kzp;
+    const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
+    const long long box = lineg / ((long long)N * N), line0 = lineg % ((long long)N * N);
     const long long sB = g.sB;
-    // zero the rows no stored mode reaches
-    for (int e = threadIdx.x; e < (N - 2 * K - 1) * 3 * L; e += T) {
-        const int n = K + 1 + e / (3 * L), c = e % (3 * L);
-        tile[n * LD + c] = cmk<cplx>(0.0, 0.0);
-    }
-    // load + pack, consecutive threads on consecutive kz
-    for (int e = threadIdx.x; e < 3 * L * Kz; e += T) {
-        const int kz = e % Kz, pc = e / Kz, p = pc / L, c = pc % L;
-        const long long off = (line0 + c) * Kzp + kz;
+    B += box * g.bB;
+    // ---- inverse: 3 packed lines per physical line, natural order into the tile
+    auto iload = [&](int vl, int n) -> cplx {
+        const int p = vl / L, l = vl % L;
+        const int kz = n <= N / 2 ? n : N - n;
+        if (kz > K) return cmk<cplx>(0.0, 0.0);
+        const long long off = (line0 + l) * Kzp + kz;
         cplx a = B[(2 * p) * sB + off];
         cplx b = B[(2 * p + 1) * sB + off];
         if (kz == 0) {
             a.y = 0;
             b.y = 0;
         }
-        // Z[kz] = a + i b,  Z[N - kz] = conj(a) + i conj(b)
-        tile[kz * LD + p * L + c] = cmk<cplx>(a.x - b.y, a.y + b.x);
-        if (kz > 0) tile[(N - kz) * LD + p * L + c] = cmk<cplx>(a.x + b.y, b.x - a.y);
+        return n <= N / 2 ? cmk<cplx>(a.x - b.y, a.y + b.x) : cmk<cplx>(a.x + b.y, b.x - a.y);
+    };
+    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
+    // ---- forward, first stage fused with u x omega (component order
+    // c0 = a1 b2 - a2 b1, c1 = a2 b0 - a0 b2, c2 = a0 b1 - a1 b0); line l
+    // becomes Nx + i Ny, line L + l becomes Nz + 0 i
+    {
+        constexpr FftPlan P = make_plan(N, MAXR);
+        constexpr int R = P.r[0];
+        constexpr int NB = N / R;
+        constexpr int TOT = NB * L;
+        constexpr int Q = (TOT + T - 1) / T;
+        cplx va[Q][R], vb[Q][R];
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int l = idx / NB, j = idx % NB;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int a = radd(j + r * NB);
+                    const cplx p0 = tile[l * LDR + a], p1 = tile[(L + l) * LDR + a], p2 = tile[(2 * L + l) * LDR + a];
+                    const real ux = p0.x, uy = p0.y, uz = p1.x, wx = p1.y, wy = p2.x, wz = p2.y;
+                    va[q][r] = cmk<cplx>(uy * wz - uz * wy, uz * wx - ux * wz);
+                    vb[q][r] = cmk<cplx>(ux * wy - uy * wx, 0.0);
+                }
+                dft<R, -1>(va[q]);
+                dft<R, -1>(vb[q]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < Q; ++q) {
+            const int idx = (int)threadIdx.x + q * T;
+            if (Q * T == TOT || idx < TOT) {
+                const int l = idx / NB, j = idx % NB;
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    const int a = radd(j * R + r);
+                    tile[l * LDR + a] = va[q][r];
+                    tile[(L + l) * LDR + a] = vb[q][r];
+                }
+            }
+        }
+        __syncthreads();
+        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1>::run(tile, tw, iload, tstore);
     }
-    __syncthreads();
-    auto tload = [&](int n, int c) -> cplx { return tile[n * LD + c]; };
-    auto tstore = [&](int n, int c, cplx v) { tile[n * LD + c] = v; };
-    TileFFT<real, N, 3 * L, T, +1>::run(tile, LD, tw, tload, tstore);
-    // u x omega, component order c0 = a1 b2 - a2 b1, c1 = a2 b0 - a0 b2, c2 = a0 b1 - a1 b0
-    for (int e = threadIdx.x; e < N * L; e += T) {
-        const int n = e / L, c = e % L;
-        const cplx p0 = tile[n * LD + c], p1 = tile[n * LD + L + c], p2 = tile[n * LD + 2 * L + c];
-        const real ux = p0.x, uy = p0.y, uz = p1.x, wx = p1.y, wy = p2.x, wz = p2.y;
-        const real nx = uy * wz - uz * wy;
-        const real ny = uz * wx - ux * wz;
-        const real nz = ux * wy - uy * wx;
-        tile[n * LD + c] = cmk<cplx>(nx, ny);
-        tile[n * LD + L + c] = cmk<cplx>(nz, 0.0);
-    }
-    __syncthreads();
-    TileFFT<real, N, 2 * L, T, -1>::run(tile, LD, tw, tload, tstore);
-    // unpack the two real transforms of line 0 and store kz <= K
-    for (int e = threadIdx.x; e < L * Kz; e += T) {
-        const int kz = e % Kz, c = e / Kz;
-        const cplx za = tile[kz * LD + c];
-        const cplx zm = tile[((N - kz) % N) * LD + c];
-        const cplx zb = tile[kz * LD + L + c];
-        const long long off = (line0 + c) * Kzp + kz;
+    // ---- unpack the two real transforms of line l and store kz <= K
+    for (int e = threadIdx.x; e < L * (K + 1); e += T) {
+        const int kz = e % (K + 1), l = e / (K + 1);
+        const cplx za = tile[l * LDR + radd(kz)];
+        const cplx zm = tile[l * LDR + radd((N - kz) % N)];
+        const cplx zb = tile[(L + l) * LDR + radd(kz)];
+        const long long off = (line0 + l) * Kzp + kz;
         // X = (Z[k] + conj Z[N-k]) / 2,  Y = (Z[k] - conj Z[N-k]) / (2i)
         B[off] = cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y));
         B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
@@ -217,7 +272,7 @@ __global__ void __launch_bounds__(T) k_p3_z_cross(Geo g, const typename CT<real>
 // ------------------------------------------------------------------- physical input
 // Forward real transform along z of a physical field u[3][N][N][N] (entry of
 // a velocity given in physical space): lines (ux + i uy) and (uz + 0i).
-template <typename real, typename ioreal, int N, int L, int T>
+template <typename real, typename ioreal, int N, int L, int T, int MAXR>
 __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                  const ioreal *__restrict__ u,
                                                  typename CT<real>::t *__restrict__ B) {
@@ -228,7 +283,7 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
     cplx *tile = tw + N;
     load_twiddles<real>(tw, twg, N);
     const int Kz = g.Kz, Kzp = g.Kzp;
-    const long long line0 = (long long)blockIdx.x * L;
+    const long long line0 = (long long)blockIdx.x * L;  // one box per launch
     const long long N3 = (long long)N * N * N;
     const long long sB = g.sB;
     for (int e = threadIdx.x; e < 2 * L * N; e += T) {
@@ -240,7 +295,7 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
     __syncthreads();
     auto tload = [&](int n, int c) -> cplx { return tile[n * LD + c]; };
     auto tstore = [&](int n, int c, cplx v) { tile[n * LD + c] = v; };
-    TileFFT<real, N, 2 * L, T, -1>::run(tile, LD, tw, tload, tstore);
+    TileFFT<real, N, 2 * L, T, -1, MAXR>::run(tile, LD, tw, tload, tstore);
     for (int e = threadIdx.x; e < L * Kz; e += T) {
         const int kz = e % Kz, c = e / Kz;
         const cplx za = tile[kz * LD + c];
@@ -254,7 +309,7 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
 }
 
 // ------------------------------------------------------------------- P4
-template <typename real, int N, int W, int T>
+template <typename real, int N, int W, int T, int MAXR>
 __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                const typename CT<real>::t *__restrict__ B,
                                                typename CT<real>::t *__restrict__ A) {
@@ -264,10 +319,10 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
     cplx *tile = tw + N;
     load_twiddles<real>(tw, twg, N);
     __syncthreads();
-    const int kz0 = blockIdx.x * W, x = blockIdx.y, f = blockIdx.z;
+    const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 3, f = blockIdx.z % 3;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = B + f * g.sB + (long long)x * N * Kzp;
-    cplx *dst = A + f * g.sA + (long long)x * Kx * Kzp;
+    const cplx *src = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
+    cplx *dst = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
@@ -278,19 +333,20 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
         const int iy = row_to_compact<N>(n, K);
         if (kz < Kz && iy >= 0) dst[(long long)iy * Kzp + kz] = v;
     };
-    TileFFT<real, N, W, T, -1>::run(tile, W, tw, load, store);
+    TileFFT<real, N, W, T, -1, MAXR>::run(tile, W, tw, load, store);
 }
 
 // ------------------------------------------------------------------- P5
 template <typename real, typename acc>
-__device__ __forceinline__ void rk_update(const UpdateArgs<real, acc> &a, long long m, int comp,
-                                          long long sS, typename CT<real>::t du) {
+__device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real, acc> &a, long long m, int comp,
+                                                          long long sS, typename CT<real>::t du) {
+    // returns the next stage input (field type): the value the next P1 transforms
     typedef typename CT<real>::t cplx;
     typedef typename CT<acc>::t cacc;
     const long long e = comp * sS + m;
     if (a.stage < 0) {
         a.dU[e] = cmk<cacc>((acc)du.x, (acc)du.y);
-        return;
+        return du;
     }
     const acc dx = (acc)du.x, dy = (acc)du.y;
     const acc adt = (acc)a.adt, bdt = (acc)a.bdt;
@@ -300,70 +356,94 @@ __device__ __forceinline__ void rk_update(const UpdateArgs<real, acc> &a, long l
     else u1 = a.U1[e];
     u1.x += adt * dx;
     u1.y += adt * dy;
+    cplx next;
     if (a.stage < 3) {
         a.U1[e] = u1;
-        a.Uout[e] = cmk<cplx>((double)(u0.x + bdt * dx), (double)(u0.y + bdt * dy));
+        next = cmk<cplx>((double)(u0.x + bdt * dx), (double)(u0.y + bdt * dy));
+        a.Uout[e] = next;
     } else {
         a.U0out[e] = u1;
-        if (a.Uout) a.Uout[e] = cmk<cplx>((double)u1.x, (double)u1.y);
+        next = cmk<cplx>((double)u1.x, (double)u1.y);
+        if (a.Uout) a.Uout[e] = next;
     }
+    return next;
 }
 
-template <typename real, typename acc, int N, int W, int T>
-__global__ void __launch_bounds__(T) k_p5_xfwd_update(Geo g, const typename CT<real>::t *__restrict__ twg,
-                                                      const typename CT<real>::t *__restrict__ A,
-                                                      UpdateArgs<real, acc> args) {
+// P5a: forward transform along x of the 3 fields, keep the Kx stored rows;
+// the result N^ (dealiased by construction) goes to a compact buffer.
+template <typename real, int N, int W, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                const typename CT<real>::t *__restrict__ A,
+                                                typename CT<real>::t *__restrict__ Nh) {
     typedef typename CT<real>::t cplx;
-    typedef typename CT<acc>::t cacc;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    cplx *res = tile + N * W;  // [3][Kx][W]: kept rows of the three transformed fields
     load_twiddles<real>(tw, twg, N);
     __syncthreads();
-    const int kz0 = blockIdx.x * W, jy = blockIdx.y;
+    const int box = blockIdx.x / 3, f = blockIdx.x % 3, kz0 = blockIdx.y * W, jy = blockIdx.z;
+    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
+    const cplx *src = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
+    cplx *dst = Nh + box * g.bB + f * g.sS + (long long)jy * Kzp;
+    auto load = [&](int n, int c) -> cplx {
+        const int kz = kz0 + c;
+        if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
+        return src[(long long)n * Kx * Kzp + kz];
+    };
+    auto store = [&](int n, int c, cplx v) {
+        const int kz = kz0 + c;
+        const int ix = row_to_compact<N>(n, K);
+        if (kz < Kz && ix >= 0) dst[(long long)ix * Kx * Kzp + kz] = v;
+    };
+    TileFFT<real, N, W, T, -1, MAXR>::run(tile, W, tw, load, store);
+}
+
+// P5b: pointwise over the stored modes: Leray projection (Eq. pressure,
+// NSfinal), viscous term and the RK4 stage (or the bare RHS / transform).
+template <typename real, typename acc>
+__global__ void k_p5b_update(Geo g, const typename CT<real>::t *__restrict__ Nh, UpdateArgs<real, acc> args) {
+    typedef typename CT<real>::t cplx;
+    typedef typename CT<acc>::t cacc;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const long long sS = g.sS;
-#pragma unroll 1
-    for (int f = 0; f < 3; ++f) {
-        const cplx *src = A + f * g.sA + (long long)jy * Kzp;
-        cplx *rf = res + f * Kx * W;
-        auto load = [&](int n, int c) -> cplx {
-            const int kz = kz0 + c;
-            if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
-            return src[(long long)n * Kx * Kzp + kz];
-        };
-        auto store = [&](int n, int c, cplx v) {
-            const int ix = row_to_compact<N>(n, K);
-            if (ix >= 0) rf[ix * W + c] = v;
-        };
-        TileFFT<real, N, W, T, -1>::run(tile, W, tw, load, store);
-    }
-    // pointwise: consecutive threads on consecutive kz
-    const real ky = (real)compact_to_k(jy, K);
-    const real nu = (real)args.nu;
-    for (int e = threadIdx.x; e < Kx * W; e += T) {
-        const int ix = e / W, c = e % W, kz = kz0 + c;
-        if (kz >= Kz) continue;
-        const cplx n0 = res[e], n1 = res[Kx * W + e], n2 = res[2 * Kx * W + e];
-        const long long m = ((long long)ix * Kx + jy) * Kzp + kz;
+    const long long total = sS * g.nb;
+    // one mode per thread (no grid-stride loop): every thread's loads are
+    // independent, which keeps enough bytes in flight
+    {
+        const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+        if (e >= total) return;
+        const long long box = e / sS, mm = e % sS;
+        const int kz = (int)(mm % Kzp);
+        if (kz >= Kz) return;
+        const long long r = mm / Kzp;
+        const int iy = (int)(r % Kx), ix = (int)(r / Kx);
+        const long long nm = box * g.bB + mm;  // N^ lives in B, state layout
+        const long long m = box * g.bS + mm;   // state element, component 0
+        const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
+        const cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
         if (args.stage == -2) {  // bare forward transform (physical input)
             args.dU[m] = cmk<cacc>(n0.x, n0.y);
             args.dU[sS + m] = cmk<cacc>(n1.x, n1.y);
             args.dU[2 * sS + m] = cmk<cacc>(n2.x, n2.y);
-            continue;
+            return;
         }
-        const real kx = (real)compact_to_k(ix, K), kzr = (real)kz;
+        const real kx = (real)compact_to_k(ix, K), ky = (real)compact_to_k(iy, K), kzr = (real)kz;
         const real k2 = kx * kx + ky * ky + kzr * kzr;
         const real inv = k2 > 0 ? (real)1 / k2 : (real)0;
-        // Leray projection: N^ - k (k . N^) / |k|^2  (Eq. pressure, NSfinal)
         const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
         const real dim = (kx * n0.y + ky * n1.y + kzr * n2.y) * inv;
         const cplx u0 = args.U[m], u1 = args.U[sS + m], u2 = args.U[2 * sS + m];
         const real vk = nu * k2;
-        rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
-        rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
-        rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+        const cplx x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
+        const cplx x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
+        const cplx x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+        if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
+            cplx ox, oy, oz;
+            curl_mode<cplx, real>(kx, ky, kzr, x0, x1, x2, ox, oy, oz);
+            args.Om[m] = ox;
+            args.Om[sS + m] = oy;
+            args.Om[2 * sS + m] = oz;
+        }
     }
 }
 

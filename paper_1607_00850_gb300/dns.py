@@ -42,6 +42,14 @@ SIGNATURES = {
     "dns_set_time": (_i, [_vp, _d, ctypes.c_long]),
     "dns_query": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _dp, _dp]),
     "dns_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "dns_ensemble_init": (_i, [_i, ctypes.POINTER(_i), _dp, _d, _i, _vp, ctypes.POINTER(_vp)]),
+    "dns_ensemble_free": (_i, [_vp]),
+    "dns_ensemble_set_velocity": (_i, [_vp, _i, _vp, _i]),
+    "dns_ensemble_get_velocity": (_i, [_vp, _i, _vp, _i]),
+    "dns_ensemble_step": (_i, [_vp, _i]),
+    "dns_ensemble_synchronize": (_i, [_vp]),
+    "dns_ensemble_energy": (_i, [_vp, _dp]),
+    "dns_ensemble_time": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -132,8 +140,8 @@ def dns_step(h: int, n: int) -> None:
 
 
 def dns_step_profiled(h: int, n: int):
-    """(per-pass device ms [5], total device ms) for n plain-launched steps."""
-    arr = (ctypes.c_double * 5)()
+    """(per-pass device ms [6], total device ms) for n plain-launched steps."""
+    arr = (ctypes.c_double * 6)()
     tot = ctypes.c_double()
     _check(load().dns_step_profiled(h, int(n), arr, ctypes.byref(tot)), "dns_step_profiled")
     return list(arr), tot.value
@@ -187,6 +195,52 @@ def dns_device_bytes(h: int) -> int:
 
 def dns_strerror(status: int) -> str:
     return load().dns_strerror(int(status)).decode()
+
+
+def dns_ensemble_init(Ns, nus, dt: float, dtype: int = DNS_F32, stream: int | None = None) -> int:
+    n = len(Ns)
+    if len(nus) != n:
+        raise ValueError("one viscosity per box")
+    Na = (ctypes.c_int * n)(*[int(x) for x in Ns])
+    nua = (ctypes.c_double * n)(*[float(x) for x in nus])
+    h = ctypes.c_void_p()
+    _check(load().dns_ensemble_init(n, Na, nua, float(dt), int(dtype), stream or None, ctypes.byref(h)),
+           "dns_ensemble_init")
+    return h.value
+
+
+def dns_ensemble_free(e: int) -> None:
+    _check(load().dns_ensemble_free(e), "dns_ensemble_free")
+
+
+def dns_ensemble_set_velocity(e: int, box: int, uhat) -> None:
+    p, dev, _keep = _buf(uhat)
+    _check(load().dns_ensemble_set_velocity(e, int(box), p, dev), "dns_ensemble_set_velocity")
+
+
+def dns_ensemble_get_velocity(e: int, box: int, out) -> None:
+    p, dev, _keep = _buf(out, writable=True)
+    _check(load().dns_ensemble_get_velocity(e, int(box), p, dev), "dns_ensemble_get_velocity")
+
+
+def dns_ensemble_step(e: int, n: int) -> None:
+    _check(load().dns_ensemble_step(e, int(n)), "dns_ensemble_step")
+
+
+def dns_ensemble_synchronize(e: int) -> None:
+    _check(load().dns_ensemble_synchronize(e), "dns_ensemble_synchronize")
+
+
+def dns_ensemble_energy(e: int, nbox: int) -> np.ndarray:
+    out = np.zeros(int(nbox))
+    _check(load().dns_ensemble_energy(e, out.ctypes.data_as(_dp)), "dns_ensemble_energy")
+    return out
+
+
+def dns_ensemble_time(e: int):
+    t, s = ctypes.c_double(), ctypes.c_long()
+    _check(load().dns_ensemble_time(e, ctypes.byref(t), ctypes.byref(s)), "dns_ensemble_time")
+    return t.value, s.value
 
 
 # ---------------------------------------------------------------- convenience
@@ -265,3 +319,52 @@ class Solver:
 
     def time(self):
         return dns_time(self.h)
+
+
+class Ensemble:
+    """Owns one ensemble handle (independent boxes advanced together)."""
+
+    def __init__(self, Ns, nus, dt: float, dtype: int = DNS_F32, stream: int | None = None):
+        self.Ns, self.nus, self.dt, self.dtype = [int(n) for n in Ns], [float(v) for v in nus], float(dt), int(dtype)
+        self.h = dns_ensemble_init(self.Ns, self.nus, dt, dtype, stream)
+
+    def close(self):
+        if self.h:
+            dns_ensemble_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_velocity(self, box: int, uhat):
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=io_complex_dtype(self.dtype))
+        dns_ensemble_set_velocity(self.h, box, uhat)
+
+    def get_velocity(self, box: int, out=None):
+        if out is None:
+            N = self.Ns[box]
+            out = np.empty((3, N, N, N // 2 + 1), io_complex_dtype(self.dtype))
+        dns_ensemble_get_velocity(self.h, box, out)
+        return out
+
+    def step(self, n: int = 1):
+        dns_ensemble_step(self.h, n)
+
+    def synchronize(self):
+        dns_ensemble_synchronize(self.h)
+
+    def energy(self) -> np.ndarray:
+        return dns_ensemble_energy(self.h, len(self.Ns))
+
+    def time(self):
+        return dns_ensemble_time(self.h)

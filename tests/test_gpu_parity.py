@@ -205,7 +205,7 @@ def test_graph_replay_equals_profiled_launches(dns):
         b.set_velocity(uh)
         a.step(3)
         passes, tot = dns.dns_step_profiled(b.h, 3)
-        assert len(passes) == 5 and tot > 0 and all(p > 0 for p in passes)
+        assert len(passes) == 6 and tot > 0 and all(p > 0 for p in passes)
         assert np.array_equal(a.get_velocity(), b.get_velocity())
         assert a.time() == b.time()
 
