@@ -151,6 +151,31 @@ int dns_ensemble_synchronize(dns_ensemble e);
 int dns_ensemble_energy(dns_ensemble e, double *E);
 int dns_ensemble_time(dns_ensemble e, double *t, long *step);
 
+/* ------------------------------------------------------------------------
+ * Diagnostics without allocation.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc where they need the
+ * numbers, such as code running while a stream is captured into a CUDA
+ * graph (allocation is not allowed during capture), callbacks and real-time
+ * loops that must stay out of the allocator, or processes whose device
+ * memory budget belongs to another framework.
+ *
+ * Kinetic energy out[0] = <|u|^2>/2 and dissipation out[1] = nu <|grad u|^2>
+ * of a full-layout spectral field uhat on the device (mesh N, I/O type of
+ * `dtype`), with the weights of dns_energy; no handle is needed.  Scratch
+ * lives in a file-scope device array of 2*1024+2 doubles (16 KB on every
+ * device that loads the library, held until the process exits), so N must be
+ * even and at most 1024 (else DNS_ERR_UNSUPPORTED; odd N is DNS_ERR_ARG).
+ * The first call on a device looks up that array's device address and should
+ * come before any stream capture; later calls only launch two kernels (plus
+ * a 16-byte copy for a host output).  All calls on a device share the array:
+ * calls that overlap on the GPU race and must be serialised by the caller.
+ * out_on_device = 1: out is device memory and the call is asynchronous on
+ * cuda_stream; 0: out is host memory and the call synchronises cuda_stream
+ * (DNS_ERR_NONFINITE if a result is not finite).  cuda_stream may be NULL.
+ * ------------------------------------------------------------------------ */
+int dns_energy_noalloc(int N, int dtype, const void *uhat, double nu, double *out, int out_on_device,
+                       void *cuda_stream);
+
 /* Human-readable name of a status code (static storage). */
 const char *dns_strerror(int status);
 

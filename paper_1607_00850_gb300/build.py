@@ -53,7 +53,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _sources_mtime():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
-    units = [(os.path.join(CSRC, "dns_api.cu"), os.path.join(BUILD, "dns_api.o"), ())]
+    units = [(os.path.join(CSRC, "dns_api.cu"), os.path.join(BUILD, "dns_api.o"), ()),
+             (os.path.join(CSRC, "dns_noalloc.cu"), os.path.join(BUILD, "dns_noalloc.o"), ())]
     for n in SIZES:
         units.append((os.path.join(CSRC, "dns_inst.cu"), os.path.join(BUILD, f"dns_inst_{n}.o"),
                       (f"-DDNS_N={n}",)))

@@ -50,6 +50,7 @@ SIGNATURES = {
     "dns_ensemble_synchronize": (_i, [_vp]),
     "dns_ensemble_energy": (_i, [_vp, _dp]),
     "dns_ensemble_time": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
+    "dns_energy_noalloc": (_i, [_i, _i, _vp, _d, _dp, _i, _vp]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -195,6 +196,24 @@ def dns_device_bytes(h: int) -> int:
 
 def dns_strerror(status: int) -> str:
     return load().dns_strerror(int(status)).decode()
+
+
+def dns_energy_noalloc(N: int, dtype: int, uhat, nu: float, out=None, stream: int | None = None):
+    """(E, eps) of a device-resident full-layout field with no device allocation.
+    ``out`` None: results come back to the host; a CUDA float64 tensor of 2
+    elements: results are written there asynchronously."""
+    p, dev, _keep = _buf(uhat)
+    if not dev:
+        raise ValueError("uhat must be device memory")
+    if out is None:
+        res = (ctypes.c_double * 2)()
+        _check(load().dns_energy_noalloc(int(N), int(dtype), p, float(nu), res, 0, stream or None),
+               "dns_energy_noalloc")
+        return res[0], res[1]
+    po, do, _k2 = _buf(out, writable=True)
+    _check(load().dns_energy_noalloc(int(N), int(dtype), p, float(nu), ctypes.cast(po, _dp), do, stream or None),
+           "dns_energy_noalloc")
+    return out
 
 
 def dns_ensemble_init(Ns, nus, dt: float, dtype: int = DNS_F32, stream: int | None = None) -> int:
