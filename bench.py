@@ -176,6 +176,8 @@ def run_ours(args, rank, world, local_rank):
 
     s = dns.Solver(N, nu, dt, dns.DNS_F32, stream=stream.cuda_stream)
     s.set_velocity(u32)
+    plan = dns.dns_autotune(s.h)       # launch shapes picked by timing on this GPU
+    shapes = {dns.PASSES[p]: dns.dns_variant_info(s.h, p, v) for p, v in enumerate(plan)}
     E0 = s.energy()
     s.step(args.warmup)
     s.synchronize()
@@ -228,6 +230,7 @@ def run_ours(args, rank, world, local_rank):
     hin = torch.from_numpy(u32).pin_memory()
     hout = torch.empty_like(hin).pin_memory()
     s = dns.Solver(N, nu, dt, dns.DNS_F32, stream=stream.cuda_stream)
+    dns.dns_set_plan(s.h, plan)
     s.set_velocity(hin)
     s.step(1)
     s.get_velocity(hout)
@@ -255,6 +258,7 @@ def run_ours(args, rank, world, local_rank):
         for name, dtype in (("fp64", dns.DNS_F64), ("f32_acc64", dns.DNS_F32_ACC64)):
             s = dns.Solver(N, nu, dt, dtype, stream=stream.cuda_stream)
             s.set_velocity(uh)
+            dns.dns_autotune(s.h)
             k64 = max(1, min(args.steps, 3))
             s.step(1)
             s.synchronize()
@@ -285,7 +289,8 @@ def run_ours(args, rank, world, local_rank):
             "data": "synthetic (seeded random-phase isotropic field)", "config": cfg,
             "parallelism": "replicas" if world > 1 else "single GPU",
             "gpu_launches": 24 * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
-            "cpu_baseline": cpu, "energy": {"initial": E0, "after_steps": E32}, **extra}
+            "cpu_baseline": cpu, "energy": {"initial": E0, "after_steps": E32},
+            "plan": {"variants": plan, "shapes (lines, radix cap, threads)": shapes}, **extra}
     return line
 
 
@@ -300,6 +305,7 @@ def ensemble_bench(args, stream):
     e = dns.Ensemble(Ns, [p[2] for p in params], 0.005, dns.DNS_F32, stream=stream.cuda_stream)
     for b, (Nb, k0, nub, seed) in enumerate(params):
         e.set_velocity(b, inputs.random_isotropic(Nb, seed=seed, k0=k0).astype(np.complex64))
+    dns.dns_ensemble_autotune(e.h)
     e.step(args.warmup)
     e.synchronize()
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

@@ -104,6 +104,18 @@ int dns_step(dns_handle h, int n);
  * Synchronises the handle's stream. */
 int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms);
 
+/* Time integrator of dns_step / dns_step_profiled.  The paper allows any
+ * integrator and uses a fourth-order Runge-Kutta method (end of Sec. 2).
+ * DNS_RK4 (default): classical RK4 on Eq. NSfinal, viscous term explicit.
+ * DNS_IFRK4: integrating-factor (Lawson) RK4: classical RK4 applied to
+ * exp(nu |k|^2 t) uhat, so the viscous decay exp(-nu |k|^2 dt) is exact
+ * and does not limit dt; stages use E1 = exp(-nu|k|^2 dt/2), E2 =
+ * exp(-nu|k|^2 dt) and the projected nonlinear term k_s:
+ *   u_{n+1} = E2 u_n + dt/6 (E2 k1 + 2 E1 k2 + 2 E1 k3 + k4).
+ * DNS_ERR_ARG for other values.  dns_rhs is not affected. */
+enum dns_integrator { DNS_RK4 = 0, DNS_IFRK4 = 1 };
+int dns_set_integrator(dns_handle h, int kind);
+
 /* Wait for the handle's queued work; reports device errors. */
 int dns_synchronize(dns_handle h);
 
@@ -129,6 +141,28 @@ int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *d
 int dns_device_bytes(dns_handle h, long long *bytes);
 
 /* ------------------------------------------------------------------------
+ * Autotuner.  Each of the five tuned passes (0: inverse x, 1: inverse y,
+ * 2: z transforms + cross product, 3: forward y, 4: forward x) is compiled
+ * in a few launch shapes: lines per block, largest radix of the FFT plan
+ * and thread count.  A "plan" picks one variant per pass; variant 0 is the
+ * default.  Every variant computes the same right-hand side (up to rounding
+ * order).
+ * ------------------------------------------------------------------------ */
+
+/* Time every compiled variant of every pass on the handle's scratch buffers
+ * (the state is not changed), keep the fastest per pass, and write the plan
+ * to plan_out[5] (may be NULL).  cache_path (may be NULL): a JSON-lines file
+ * keyed by GPU name, N, dtype and box count; a matching entry is applied
+ * without timing, and a new result is appended.  Synchronising.  The next
+ * dns_step recaptures its graph. */
+int dns_autotune(dns_handle h, const char *cache_path, int *plan_out);
+int dns_get_plan(dns_handle h, int *plan);
+/* DNS_ERR_UNSUPPORTED if a variant is not compiled for this N and dtype. */
+int dns_set_plan(dns_handle h, const int *plan);
+/* Shape of one variant: lines per block, radix cap, threads per block. */
+int dns_variant_info(dns_handle h, int pass, int variant, int *lines, int *max_radix, int *threads);
+
+/* ------------------------------------------------------------------------
  * Batched ensemble: many independent boxes (each its own N, nu and initial
  * field; one dt and dtype) advanced together.  Boxes of one N share every
  * kernel launch (the grid covers all of them), and one RK4 step of every box
@@ -150,6 +184,8 @@ int dns_ensemble_synchronize(dns_ensemble e);
  * DNS_ERR_NONFINITE if any is not finite. */
 int dns_ensemble_energy(dns_ensemble e, double *E);
 int dns_ensemble_time(dns_ensemble e, double *t, long *step);
+/* Autotune every size class of the ensemble (as dns_autotune). */
+int dns_ensemble_autotune(dns_ensemble e, const char *cache_path);
 
 /* ------------------------------------------------------------------------
  * Diagnostics without allocation.  The paper has no counterpart: this is a

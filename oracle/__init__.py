@@ -21,6 +21,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC_LES = os.path.join(_HERE, "oracle_les.c")
 LIB_PATH = os.path.join(_HERE, "liboracle.so")
 
 _dp = ctypes.POINTER(ctypes.c_double)
@@ -31,7 +32,7 @@ def build(out_path: str = LIB_PATH, mutant: int = 0, openmp: bool = True) -> str
 
     ``mutant`` > 0 plants the numbered deliberate mistake (tests only)."""
     cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-D_GNU_SOURCE",
-           f"-DOR_MUTANT={int(mutant)}", "-I", _HERE, _SRC, "-o", out_path, "-lm"]
+           f"-DOR_MUTANT={int(mutant)}", "-I", _HERE, _SRC, _SRC_LES, "-o", out_path, "-lm"]
     if openmp:
         cmd.insert(1, "-fopenmp")
     tmp = out_path + f".tmp{os.getpid()}"
@@ -45,7 +46,7 @@ def _stale() -> bool:
     if not os.path.exists(LIB_PATH):
         return True
     t = os.path.getmtime(LIB_PATH)
-    return any(os.path.getmtime(os.path.join(_HERE, f)) > t for f in ("oracle.c", "oracle.h"))
+    return any(os.path.getmtime(os.path.join(_HERE, f)) > t for f in ("oracle.c", "oracle_les.c", "oracle.h"))
 
 
 class Oracle:
@@ -63,9 +64,16 @@ class Oracle:
             "or_nonlinear": [ctypes.c_int, _dp, _dp],
             "or_rhs": [ctypes.c_int, ctypes.c_double, _dp, _dp],
             "or_rk4": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp],
+            "or_rk4_if": [ctypes.c_int, ctypes.c_double, ctypes.c_double, ctypes.c_int, _dp],
             "or_energy": [ctypes.c_int, _dp, _dp],
             "or_dissipation": [ctypes.c_int, ctypes.c_double, _dp, _dp],
             "or_spectrum": [ctypes.c_int, _dp, _dp, ctypes.c_int],
+            "or_conv3d_fwd": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp],
+            "or_conv3d_bwd": [ctypes.c_int, ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, _dp, _dp, _dp],
+            "or_gelu": [ctypes.c_long, _dp, _dp, _dp],
+            "or_net": [ctypes.c_int] + [_dp] * 16,
+            "or_les_inputs": [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp],
+            "or_rhs_les": [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp],
         }.items():
             f = getattr(lib, name)
             f.argtypes = args
@@ -160,6 +168,12 @@ class Oracle:
                                     self._ptr(u.view(np.float64))), "or_rk4")
         return u
 
+    def rk4_if(self, uhat, nu: float, dt: float, nsteps: int) -> np.ndarray:
+        u = self._spec(uhat).copy()
+        self._check(self.lib.or_rk4_if(u.shape[1], float(nu), float(dt), int(nsteps),
+                                       self._ptr(u.view(np.float64))), "or_rk4_if")
+        return u
+
     # -- diagnostics -------------------------------------------------------
     def energy(self, uhat) -> float:
         uhat = self._spec(uhat)
@@ -175,6 +189,68 @@ class Oracle:
                                             self._ptr(uhat.view(np.float64)), ctypes.byref(e)),
                     "or_dissipation")
         return e.value
+
+    # -- learned closure of a coarse LES ------------------------------------
+    def conv3d_fwd(self, x, w, b=None) -> np.ndarray:
+        x = np.ascontiguousarray(x, np.float64)
+        w = np.ascontiguousarray(w, np.float64)
+        cin, n = x.shape[0], x.shape[1]
+        cout = w.shape[0]
+        assert w.shape == (cout, cin, 27)
+        y = np.empty((cout, n, n, n))
+        bp = self._ptr(np.ascontiguousarray(b, np.float64)) if b is not None else None
+        self._check(self.lib.or_conv3d_fwd(n, cin, cout, self._ptr(x), self._ptr(w), bp, self._ptr(y)),
+                    "or_conv3d_fwd")
+        return y
+
+    def conv3d_bwd(self, x, w, dy):
+        x, w, dy = (np.ascontiguousarray(a, np.float64) for a in (x, w, dy))
+        cin, n, cout = x.shape[0], x.shape[1], w.shape[0]
+        dx = np.empty_like(x)
+        dw = np.zeros_like(w)
+        db = np.zeros(cout)
+        self._check(self.lib.or_conv3d_bwd(n, cin, cout, self._ptr(x), self._ptr(w), self._ptr(dy),
+                                           self._ptr(dx), self._ptr(dw), self._ptr(db)), "or_conv3d_bwd")
+        return dx, dw, db
+
+    def gelu(self, x):
+        x = np.ascontiguousarray(x, np.float64)
+        y, d = np.empty_like(x), np.empty_like(x)
+        self._check(self.lib.or_gelu(x.size, self._ptr(x), self._ptr(y), self._ptr(d)), "or_gelu")
+        return y, d
+
+    def net(self, g, params, target=None, grads=False):
+        """params = (w1, b1, w2, b2, w3, b3); returns (out, loss, grads or None)."""
+        g = np.ascontiguousarray(g, np.float64)
+        n = g.shape[1]
+        ps = [np.ascontiguousarray(p, np.float64) for p in params]
+        out = np.empty((6, n, n, n))
+        loss = ctypes.c_double(0.0)
+        tp = self._ptr(np.ascontiguousarray(target, np.float64)) if target is not None else None
+        gs = [np.zeros_like(p) for p in ps] if grads else None
+        gp = [self._ptr(x) for x in gs] if grads else [None] * 6
+        self._check(self.lib.or_net(n, self._ptr(g), tp, *[self._ptr(p) for p in ps], self._ptr(out),
+                                    ctypes.cast(ctypes.pointer(loss), _dp) if target is not None else None,
+                                    *gp), "or_net")
+        return out, (loss.value if target is not None else None), gs
+
+    def les_inputs(self, uhat, n: int):
+        uhat = self._spec(uhat)
+        N = uhat.shape[1]
+        ub = np.empty((3, n, n, n // 2 + 1), np.complex128)
+        g = np.empty((9, n, n, n))
+        tau = np.empty((6, n, n, n))
+        self._check(self.lib.or_les_inputs(N, self._ptr(uhat.view(np.float64)), n, self._ptr(ub.view(np.float64)),
+                                           self._ptr(g), self._ptr(tau)), "or_les_inputs")
+        return ub, g, tau
+
+    def rhs_les(self, ubar, nu: float, tau) -> np.ndarray:
+        ubar = self._spec(ubar)
+        tau = np.ascontiguousarray(tau, np.float64)
+        out = np.empty_like(ubar)
+        self._check(self.lib.or_rhs_les(ubar.shape[1], float(nu), self._ptr(ubar.view(np.float64)),
+                                        self._ptr(tau), self._ptr(out.view(np.float64))), "or_rhs_les")
+        return out
 
     def spectrum(self, uhat, nshells: int | None = None) -> np.ndarray:
         uhat = self._spec(uhat)

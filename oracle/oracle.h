@@ -50,11 +50,34 @@ int or_nonlinear(int N, const double *uhat, double *nhat);
 int or_rhs(int N, double nu, const double *uhat, double *duhat);
 /* nsteps classical RK4 steps of Eq. NSfinal, in place on uhat. */
 int or_rk4(int N, double nu, double dt, int nsteps, double *uhat);
+/* nsteps integrating-factor (Lawson) RK4 steps: exact viscous decay,
+ * classical RK4 on the nonlinear term; in place on uhat. */
+int or_rk4_if(int N, double nu, double dt, int nsteps, double *uhat);
 
 /* Diagnostics of a spectral field (half-spectrum Parseval weights). */
 int or_energy(int N, const double *uhat, double *E);
 int or_dissipation(int N, double nu, const double *uhat, double *eps);
 int or_spectrum(int N, const double *uhat, double *Ek, int nshells);
+
+/* ---- learned subgrid closure of a coarse LES (oracle_les.c) ---------- */
+/* Periodic 3x3x3 cross-correlation y[o] = b[o] + sum_{c,t} w[o][c][t] x[c](p + off(t)),
+ * tap t = 9 tx + 3 ty + tz at offset (tx-1, ty-1, tz-1); [C][n][n][n] layouts. */
+int or_conv3d_fwd(int n, int cin, int cout, const double *x, const double *w, const double *b, double *y);
+/* Gradients of a convolution: dx (optional, overwritten), dw and db (accumulated). */
+int or_conv3d_bwd(int n, int cin, int cout, const double *x, const double *w, const double *dy, double *dx,
+                  double *dw, double *db);
+/* GELU(x) = x (1 + erf(x/sqrt 2))/2 and its derivative (either output optional). */
+int or_gelu(long count, const double *x, double *y, double *dydx);
+/* 3-layer closure network (9 -> 32 -> 32 -> 6, GELU): output, mean-squared
+ * loss against target, and accumulated weight/bias gradients (optional). */
+int or_net(int n, const double *g, const double *target, const double *w1, const double *b1, const double *w2,
+           const double *b2, const double *w3, const double *b3, double *out, double *loss, double *gw1,
+           double *gb1, double *gw2, double *gb2, double *gw3, double *gb3);
+/* Sharp-cutoff filter of an N^3 DNS field to an n^3 LES mesh: ubar_hat,
+ * gradients g[9][n^3] (g[3i+j] = d_j ubar_i), stresses tau[6][n^3]. */
+int or_les_inputs(int N, const double *uhat, int n, double *ubar_hat, double *g, double *tau);
+/* LES right-hand side: Eq. NSfinal on ubar plus P(m (-i k_j tau_ij^)). */
+int or_rhs_les(int n, double nu, const double *ubar_hat, const double *tau, double *duhat);
 
 #ifdef __cplusplus
 }

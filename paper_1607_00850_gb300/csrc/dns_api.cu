@@ -54,6 +54,8 @@ struct dns_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long bytes = 0;
+    int plan[5] = {0, 0, 0, 0, 0};  // variant of P1, P2, P3, P4, P5a
+    int integrator = 0;             // DNS_RK4 or DNS_IFRK4
 };
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -151,10 +153,10 @@ static cudaError_t acc_to_full(dns_ctx *h, const void *cmp, void *full) {
 static cudaError_t launch_front(dns_ctx *h, const void *Uin, const void *Omin) {
     cudaError_t e;
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
-    if ((e = h->ps.p1(h->g, h->tw, Uin, Omin, h->A, scale, h->stream)) != cudaSuccess) return e;
-    if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
-    if ((e = h->ps.p3(h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
-    return h->ps.p4(h->g, h->tw, h->B, h->A, h->stream);
+    if ((e = h->ps.p1[h->plan[0]](h->g, h->tw, Uin, Omin, h->A, scale, h->stream)) != cudaSuccess) return e;
+    if ((e = h->ps.p2[h->plan[1]](h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+    if ((e = h->ps.p3[h->plan[2]](h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
+    return h->ps.p4[h->plan[3]](h->g, h->tw, h->B, h->A, h->stream);
 }
 
 static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
@@ -170,7 +172,9 @@ static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
     a.nu_box = h->nu_box;
     a.adt = RK_A[s] * h->dt;
     a.bdt = s < 3 ? RK_B[s] * h->dt : 0.0;
+    a.dt = h->dt;
     a.stage = s;
+    a.ifrk = h->integrator == DNS_IFRK4;
     return a;
 }
 
@@ -185,15 +189,15 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
     for (int s = 0; s < 4; ++s) {
         dns::UpdateArgsErased a = stage_args(h, s);
-        if ((e = h->ps.p1(h->g, h->tw, a.U, h->Om, h->A, scale, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p1[h->plan[0]](h->g, h->tw, a.U, h->Om, h->A, scale, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p2(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p2[h->plan[1]](h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p3(h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p3[h->plan[2]](h->g, h->tw, h->B, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p4(h->g, h->tw, h->B, h->A, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p4[h->plan[3]](h->g, h->tw, h->B, h->A, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+        if ((e = h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
         if ((e = h->ps.p5b(h->g, h->B, a, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
@@ -353,7 +357,11 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, nb * 3 * g.sS * h->cacc, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, nb * 3 * g.sS * h->cacc, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->Om, 0, nb * 3 * g.sS * h->creal, h->stream);
-    if (e == cudaSuccess) e = h->ps.prepare();
+    for (int v = 0; v < dns::PassSet::NCOLV && e == cudaSuccess; ++v)
+        if (h->ps.prep_col[v]) e = h->ps.prep_col[v]();
+    for (int v = 0; v < dns::PassSet::NP3V && e == cudaSuccess; ++v)
+        if (h->ps.prep_p3[v]) e = h->ps.prep_p3[v]();
+    if (e == cudaSuccess) e = h->ps.prep_misc();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
         g_last_cuda = e;
@@ -416,11 +424,11 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
         src = h->io;
     }
     CK(h->ps.zfwd(h->g, h->tw, src, h->B, h->stream));
-    CK(h->ps.p4(h->g, h->tw, h->B, h->A, h->stream));
+    CK(h->ps.p4[h->plan[3]](h->g, h->tw, h->B, h->A, h->stream));
     dns::UpdateArgsErased a{};
     a.dU = h->rout;
     a.stage = -2;
-    CK(h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream));
+    CK(h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream));
     CK(h->ps.p5b(h->g, h->B, a, h->stream));
     const long long n = 3 * h->g.sS;
     CK(cudaMemcpyAsync(h->U0, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
@@ -458,7 +466,7 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
     a.dU = h->rout;
     a.nu = h->nu;
     a.stage = -1;
-    CK(h->ps.p5a(h->g, h->tw, h->A, h->B, h->stream));
+    CK(h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream));
     CK(h->ps.p5b(h->g, h->B, a, h->stream));
     if (on_device) {
         CK(acc_to_full(h, h->rout, duhat_out));
@@ -601,6 +609,185 @@ int dns_query(dns_handle h, int *N, int *dtype, int *kmax, double *nu, double *d
 int dns_device_bytes(dns_handle h, long long *bytes) {
     if (!h || !bytes) return DNS_ERR_ARG;
     *bytes = h->bytes;
+    return DNS_OK;
+}
+
+// --------------------------------------------------------------- autotuner
+}  // extern "C"
+
+static void drop_graph(dns_ctx *h) {
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+}
+
+static bool variant_exists(const dns_ctx *h, int pass, int v) {
+    if (pass == 2) return v >= 0 && v < dns::PassSet::NP3V && h->ps.p3[v];
+    if (pass < 0 || pass > 4) return false;
+    return v >= 0 && v < dns::PassSet::NCOLV && h->ps.p1[v];
+}
+
+static int variant_count(int pass) { return pass == 2 ? dns::PassSet::NP3V : dns::PassSet::NCOLV; }
+
+// Mean device time of `reps` launches of one variant of one pass on the
+// handle's scratch buffers (A, B); the state is only read.
+static cudaError_t time_variant(dns_ctx *h, int pass, int v, int reps, float *ms) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    const double scale = 1.0 / ((double)h->N * h->N * h->N);
+    auto launch = [&]() -> cudaError_t {
+        switch (pass) {
+            case 0: return h->ps.p1[v](h->g, h->tw, h->U, h->Om, h->A, scale, h->stream);
+            case 1: return h->ps.p2[v](h->g, h->tw, h->A, h->B, h->stream);
+            case 2: return h->ps.p3[v](h->g, h->tw, h->B, h->stream);
+            case 3: return h->ps.p4[v](h->g, h->tw, h->B, h->A, h->stream);
+            default: return h->ps.p5a[v](h->g, h->tw, h->A, h->B, h->stream);
+        }
+    };
+    if (e == cudaSuccess) e = launch();  // warm-up
+    if (e == cudaSuccess) e = cudaEventRecord(e0, h->stream);
+    for (int i = 0; i < reps && e == cudaSuccess; ++i) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(e1, h->stream);
+    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    *ms = t / reps;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    return e;
+}
+
+static void device_name(char *out, size_t n) {
+    int dev = 0;
+    cudaDeviceProp prop;
+    out[0] = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaGetDeviceProperties(&prop, dev) == cudaSuccess) {
+        size_t i = 0;
+        for (; i + 1 < n && prop.name[i]; ++i) out[i] = prop.name[i] == '"' ? '\'' : prop.name[i];
+        out[i] = 0;
+    }
+}
+
+// Cache lines: {"gpu": "<name>", "N": n, "dtype": d, "nb": b, "plan": [p1, p2, p3, p4, p5a]}
+static bool cache_lookup(const char *path, const char *gpu, const dns_ctx *h, int *plan) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return false;
+    char line[1024];
+    bool found = false;
+    while (!found && std::fgets(line, sizeof line, f)) {
+        static const char kGpuKey[] = "\"gpu\": \"";
+        const char *g = std::strstr(line, kGpuKey);
+        const char *q = std::strstr(line, "\"N\":");
+        if (!g || !q) continue;
+        g += sizeof(kGpuKey) - 1;
+        const char *ge = std::strchr(g, '"');
+        if (!ge || (size_t)(ge - g) != std::strlen(gpu) || std::strncmp(g, gpu, ge - g) != 0) continue;
+        int N = 0, dt = 0, nb = 0, p[5];
+        if (std::sscanf(q, "\"N\": %d, \"dtype\": %d, \"nb\": %d, \"plan\": [%d, %d, %d, %d, %d]", &N, &dt, &nb, &p[0],
+                        &p[1], &p[2], &p[3], &p[4]) != 8)
+            continue;
+        if (N != h->N || dt != h->dtype || nb != h->g.nb) continue;
+        bool ok = true;
+        for (int i = 0; i < 5; ++i) ok = ok && variant_exists(h, i, p[i]);
+        if (ok) {
+            for (int i = 0; i < 5; ++i) plan[i] = p[i];
+            found = true;
+        }
+    }
+    std::fclose(f);
+    return found;
+}
+
+static int autotune_ctx(dns_ctx *h, const char *cache_path, int reps) {
+    char gpu[256];
+    device_name(gpu, sizeof gpu);
+    int plan[5];
+    if (cache_path && cache_lookup(cache_path, gpu, h, plan)) {
+        for (int i = 0; i < 5; ++i) h->plan[i] = plan[i];
+        drop_graph(h);
+        return DNS_OK;
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    float best_ms[5];
+    for (int pass = 0; pass < 5; ++pass) {
+        int best = 0;
+        float bt = 1e30f;
+        for (int v = 0; v < variant_count(pass); ++v) {
+            if (!variant_exists(h, pass, v)) continue;
+            float ms = 0.f;
+            CK(time_variant(h, pass, v, reps, &ms));
+            if (ms < bt) {
+                bt = ms;
+                best = v;
+            }
+        }
+        plan[pass] = best;
+        best_ms[pass] = bt;
+    }
+    for (int i = 0; i < 5; ++i) h->plan[i] = plan[i];
+    drop_graph(h);
+    if (cache_path) {
+        FILE *f = std::fopen(cache_path, "a");
+        if (f) {
+            std::fprintf(f,
+                         "{\"gpu\": \"%s\", \"N\": %d, \"dtype\": %d, \"nb\": %d, \"plan\": [%d, %d, %d, %d, %d], "
+                         "\"ms\": [%.4f, %.4f, %.4f, %.4f, %.4f]}\n",
+                         gpu, h->N, h->dtype, h->g.nb, plan[0], plan[1], plan[2], plan[3], plan[4], best_ms[0],
+                         best_ms[1], best_ms[2], best_ms[3], best_ms[4]);
+            std::fclose(f);
+        }
+    }
+    return DNS_OK;
+}
+
+extern "C" {
+
+int dns_autotune(dns_handle h, const char *cache_path, int *plan_out) {
+    if (!h) return DNS_ERR_ARG;
+    int rc = autotune_ctx(h, cache_path, 3);
+    if (!rc && plan_out)
+        for (int i = 0; i < 5; ++i) plan_out[i] = h->plan[i];
+    return rc;
+}
+
+int dns_set_integrator(dns_handle h, int kind) {
+    if (!h || (kind != DNS_RK4 && kind != DNS_IFRK4)) return DNS_ERR_ARG;
+    if (kind != h->integrator) {
+        h->integrator = kind;
+        drop_graph(h);
+    }
+    return DNS_OK;
+}
+
+int dns_get_plan(dns_handle h, int *plan) {
+    if (!h || !plan) return DNS_ERR_ARG;
+    for (int i = 0; i < 5; ++i) plan[i] = h->plan[i];
+    return DNS_OK;
+}
+
+int dns_set_plan(dns_handle h, const int *plan) {
+    if (!h || !plan) return DNS_ERR_ARG;
+    for (int i = 0; i < 5; ++i)
+        if (!variant_exists(h, i, plan[i])) return DNS_ERR_UNSUPPORTED;
+    for (int i = 0; i < 5; ++i) h->plan[i] = plan[i];
+    drop_graph(h);
+    return DNS_OK;
+}
+
+int dns_variant_info(dns_handle h, int pass, int variant, int *lines, int *max_radix, int *threads) {
+    if (!h || pass < 0 || pass > 4) return DNS_ERR_ARG;
+    if (!variant_exists(h, pass, variant)) return DNS_ERR_UNSUPPORTED;
+    if (pass == 2) {
+        if (lines) *lines = h->ps.p3_l[variant];
+        if (max_radix) *max_radix = h->ps.p3_r[variant];
+        if (threads) *threads = h->ps.p3_t[variant];
+    } else {
+        if (lines) *lines = h->ps.col_w[variant];
+        if (max_radix) *max_radix = h->ps.col_r[variant];
+        if (threads) *threads = h->ps.col_t[variant];
+    }
     return DNS_OK;
 }
 
@@ -759,6 +946,19 @@ int dns_ensemble_time(dns_ensemble e, double *t, long *step) {
     if (!e) return DNS_ERR_ARG;
     if (t) *t = e->t;
     if (step) *step = e->step;
+    return DNS_OK;
+}
+
+int dns_ensemble_autotune(dns_ensemble e, const char *cache_path) {
+    if (!e) return DNS_ERR_ARG;
+    for (dns_ctx *h : e->cls) {
+        int rc = autotune_ctx(h, cache_path, 3);
+        if (rc) return rc;
+    }
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    e->exec = nullptr;
+    e->graph = nullptr;
     return DNS_OK;
 }
 

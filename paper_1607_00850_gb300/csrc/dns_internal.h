@@ -13,33 +13,39 @@ struct UpdateArgsErased {
     const void *U, *U0;
     void *U1, *Uout, *U0out, *dU;
     void *Om;  // curl of the next stage input out, or nullptr
-    double nu, adt, bdt;
+    double nu, adt, bdt, dt;
     const double *nu_box;  // per-box viscosity for batched boxes, or nullptr
     int stage;  // 0..3 RK4 stage, -1 right-hand side only, -2 raw forward transform
+    int ifrk;   // 1: integrating-factor RK4
 };
 
-// Launch shapes and entry points for one (N, dtype).  `real` is the field
-// type (float or double); `acc` the RK4 state type.
+typedef cudaError_t (*ColP1)(const Geo &, const void *tw, const void *U, const void *Om, void *A, double scale,
+                             cudaStream_t);
+typedef cudaError_t (*ColPass)(const Geo &, const void *tw, const void *src, void *dst, cudaStream_t);
+typedef cudaError_t (*ZPass)(const Geo &, const void *tw, void *B, cudaStream_t);
+typedef cudaError_t (*Prep)();
+
+// Entry points for one (N, dtype): every compiled variant of each tuned pass
+// (nullptr where a shape is not compiled) and the untuned kernels.
 struct PassSet {
-    int W, T;    // P1, P2, P4, P5a: columns per tile, threads
-    int L3, T3;  // P3: lines per block, threads
-    size_t smem_col, smem_p3;
-    cudaError_t (*p1)(const Geo &, const void *tw, const void *U, const void *Om, void *A, double scale,
-                      cudaStream_t);
-    // Om = i k x U on the stored modes (all boxes of the context)
-    cudaError_t (*curl)(const Geo &, const void *U, void *Om, cudaStream_t);
-    cudaError_t (*p2)(const Geo &, const void *tw, const void *A, void *B, cudaStream_t);
-    cudaError_t (*p3)(const Geo &, const void *tw, void *B, cudaStream_t);
-    cudaError_t (*p4)(const Geo &, const void *tw, const void *B, void *A, cudaStream_t);
-    cudaError_t (*p5a)(const Geo &, const void *tw, const void *A, void *Nh, cudaStream_t);
-    cudaError_t (*p5b)(const Geo &, const void *Nh, const UpdateArgsErased &, cudaStream_t);
+    static constexpr int NCOLV = 3;  // column-pass variants (W, RC)
+    static constexpr int NP3V = 4;   // z-pass variants (L, R3)
+    ColP1 p1[NCOLV] = {};
+    ColPass p2[NCOLV] = {}, p4[NCOLV] = {}, p5a[NCOLV] = {};
+    Prep prep_col[NCOLV] = {};
+    int col_w[NCOLV] = {}, col_r[NCOLV] = {}, col_t[NCOLV] = {};
+    ZPass p3[NP3V] = {};
+    Prep prep_p3[NP3V] = {};
+    int p3_l[NP3V] = {}, p3_r[NP3V] = {}, p3_t[NP3V] = {};
+    cudaError_t (*p5b)(const Geo &, const void *Nh, const UpdateArgsErased &, cudaStream_t) = nullptr;
     // physical real lines [3][N][N][N] (io real type) -> B fields 0..2, kz <= K
-    cudaError_t (*zfwd)(const Geo &, const void *tw, const void *u, void *B, cudaStream_t);
-    // raise shared-memory limits of all kernels above; call before any launch
-    cudaError_t (*prepare)();
+    cudaError_t (*zfwd)(const Geo &, const void *tw, const void *u, void *B, cudaStream_t) = nullptr;
+    // Om = i k x U on the stored modes (all boxes of the context)
+    cudaError_t (*curl)(const Geo &, const void *U, void *Om, cudaStream_t) = nullptr;
+    Prep prep_misc = nullptr;
 };
 
-// dtype: 0 = F32, 1 = F64, 2 = F32_ACC64.  io_double: physical input type.
+// dtype: 0 = F32, 1 = F64, 2 = F32_ACC64.
 typedef bool (*PassGetter)(int dtype, PassSet *out);
 
 }  // namespace dns

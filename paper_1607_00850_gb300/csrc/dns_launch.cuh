@@ -1,6 +1,15 @@
 // Launch shapes and host launchers for one mesh size N.  Compiled once per
 // supported N (dns_inst.cu with -DDNS_N=...), so the kernel units build in
 // parallel.
+//
+// Every tuned pass is compiled in a few shapes ("variants"); the autotuner
+// times them on the device and picks one per pass (variant 0 is the default).
+//   column passes (P1, P2, P4, P5a): W lines per tile x radix cap RC
+//   z pass (P3):                      L lines per block x radix cap R3
+// The thread count follows from a register budget per thread and stage (BUD:
+// 32 complex floats or 16 complex doubles): T = W N / BUD rounded up to 32.
+// Shapes whose threads exceed 1024 or whose shared memory exceeds the 227 KB
+// a block may use are not compiled; meshes below 64 compile only variant 0.
 #pragma once
 
 #include "dns_internal.h"
@@ -8,28 +17,73 @@
 
 namespace dns {
 
-// Launch shapes.  Column passes use 128-byte tile rows (16 complex floats or
-// 8 complex doubles); P3 packs L lines of 3 field pairs.  BUD = register
-// budget per thread and stage (32 complex floats or 16 complex doubles),
-// which fixes the thread count; RC / R3 cap the radix of the column passes
-// and of P3 (larger radices mean fewer shared-memory round trips).
-template <typename real, int N> struct Shape {
-    static constexpr bool f32 = sizeof(real) == 4;
-    static constexpr int BUD = f32 ? 32 : 16;
-    static constexpr int RC = f32 ? 16 : 8;
-    static constexpr int R3 = f32 ? 32 : 16;
-    static constexpr int W = f32 ? 16 : 8;
-    static constexpr int T = tile_threads(N, W, BUD);
-    static constexpr int pow2 = (N & -N);  // largest power of two dividing N
-    static constexpr int L3w = f32 ? (N >= 768 ? 4 : 8) : (N >= 768 ? 2 : 4);
-    static constexpr int L3 = L3w < pow2 ? L3w : pow2;
-    static constexpr int T3 = tile_threads(N, 3 * L3, BUD);
-    static constexpr int LZ = L3;  // physical-input z pass
-    static constexpr int TZ = tile_threads(N, 2 * LZ, BUD);
+constexpr size_t kMaxSmem = 227 * 1024;
+
+template <typename real> struct VariantTable;
+template <> struct VariantTable<float> {
+    static constexpr int BUD = 32;
+    static constexpr int colW[3] = {16, 32, 16};
+    static constexpr int colR[3] = {16, 16, 8};
+    static constexpr int p3L[4] = {8, 4, 16, 8};
+    static constexpr int p3R[4] = {32, 32, 32, 16};
+};
+template <> struct VariantTable<double> {
+    static constexpr int BUD = 16;
+    static constexpr int colW[3] = {8, 16, 8};
+    static constexpr int colR[3] = {8, 8, 16};
+    static constexpr int p3L[4] = {4, 2, 8, 4};
+    static constexpr int p3R[4] = {16, 16, 16, 8};
+};
+
+__host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
+    return (((N * W + BUD - 1) / BUD + 31) / 32) * 32;
+}
+__host__ __device__ constexpr int at_least_32(int t) { return t < 32 ? 32 : t; }
+
+template <typename real, int N, int V> struct ColShape {
+    typedef VariantTable<real> VT;
+    static constexpr int W = VT::colW[V];
+    static constexpr int RC = VT::colR[V];
+    static constexpr int T = at_least_32(raw_threads(N, W, VT::BUD));
     typedef typename CT<real>::t cplx;
-    static constexpr size_t smem_col = sizeof(cplx) * (size_t)(N + N * W);
-    static constexpr size_t smem_p3 = sizeof(cplx) * (size_t)(N + 3 * L3 * row_ld(N));
-    static constexpr size_t smem_zf = sizeof(cplx) * (size_t)(N + N * (2 * LZ + 1));
+    static constexpr size_t smem = sizeof(cplx) * (size_t)(N + N * W);
+    static constexpr bool valid = (V == 0 || N >= 64) && T <= 1024 && smem <= kMaxSmem;
+};
+
+__host__ __device__ constexpr int pow2_floor(int x) {
+    int p = 1;
+    while (2 * p <= x) p *= 2;
+    return p;
+}
+
+// P3 keeps at most 512 threads per block (at least 128 registers each); the
+// default variant is clamped to that, the others are only compiled if their
+// L fits as asked.
+template <typename real, int N, int V> struct P3Shape {
+    typedef VariantTable<real> VT;
+    static constexpr int pow2 = (N & -N);  // largest power of two dividing N
+    static constexpr int lmax = pow2_floor(512 * VT::BUD / (3 * N)) < 1 ? 1 : pow2_floor(512 * VT::BUD / (3 * N));
+    static constexpr int Lreq = VT::p3L[V];
+    static constexpr int L0 = Lreq < pow2 ? Lreq : pow2;
+    static constexpr int L = (V == 0 && L0 > lmax) ? lmax : L0;
+    static constexpr int R3 = VT::p3R[V];
+    static constexpr int T = at_least_32(raw_threads(N, 3 * L, VT::BUD));
+    typedef typename CT<real>::t cplx;
+    static constexpr size_t smem = sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
+    static constexpr bool valid =
+        (V == 0 || (N >= 64 && Lreq <= lmax && Lreq <= pow2)) && T <= 1024 && smem <= kMaxSmem;
+};
+
+// physical-input z pass (column-mapped, not tuned)
+template <typename real, int N> struct ZShape {
+    typedef VariantTable<real> VT;
+    static constexpr int pow2 = (N & -N);
+    static constexpr int Lw = sizeof(real) == 4 ? 8 : 4;
+    static constexpr int LZ = Lw < pow2 ? Lw : pow2;
+    static constexpr int T = at_least_32(raw_threads(N, 2 * LZ, VT::BUD));
+    static constexpr int R = sizeof(real) == 4 ? 32 : 16;
+    typedef typename CT<real>::t cplx;
+    static constexpr size_t smem = sizeof(cplx) * (size_t)(N + N * (2 * LZ + 1));
 };
 
 template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
@@ -39,52 +93,70 @@ template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
 
 static inline int cdiv(int a, int b) { return (a + b - 1) / b; }
 
-template <typename real, int N> struct ColLaunch {
-    typedef Shape<real, N> S;
+template <typename real, int N, int V> struct ColLaunch {
+    typedef ColShape<real, N, V> S;
     typedef typename CT<real>::t cplx;
-
     static cudaError_t p1(const Geo &g, const void *tw, const void *U, const void *Om, void *A, double scale,
                           cudaStream_t st) {
-        auto k = k_p1_xinv<real, N, S::W, S::T, S::RC>;
         dim3 grid(6 * g.nb, cdiv(g.Kz, S::W), g.Kx);
-        k<<<grid, S::T, S::smem_col, st>>>(g, (const cplx *)tw, (const cplx *)U, (const cplx *)Om, (cplx *)A,
-                                           (real)scale);
+        k_p1_xinv<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(
+            g, (const cplx *)tw, (const cplx *)U, (const cplx *)Om, (cplx *)A, (real)scale);
         return cudaGetLastError();
+    }
+    static cudaError_t p2(const Geo &g, const void *tw, const void *A, void *B, cudaStream_t st) {
+        dim3 grid(cdiv(g.Kz, S::W), N, 6 * g.nb);
+        k_p2_yinv<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)A,
+                                                                           (cplx *)B);
+        return cudaGetLastError();
+    }
+    static cudaError_t p4(const Geo &g, const void *tw, const void *B, void *A, cudaStream_t st) {
+        dim3 grid(cdiv(g.Kz, S::W), N, 3 * g.nb);
+        k_p4_yfwd<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)B,
+                                                                           (cplx *)A);
+        return cudaGetLastError();
+    }
+    static cudaError_t p5a(const Geo &g, const void *tw, const void *A, void *Nh, cudaStream_t st) {
+        dim3 grid(3 * g.nb, cdiv(g.Kz, S::W), g.Kx);
+        k_p5a_xfwd<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+                                                                            (const cplx *)A, (cplx *)Nh);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare() {
+        cudaError_t e;
+        if ((e = set_smem(k_p1_xinv<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_p2_yinv<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_p4_yfwd<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
+        return set_smem(k_p5a_xfwd<real, N, S::W, S::T, S::RC>, S::smem);
+    }
+};
+
+template <typename real, int N, int V> struct P3Launch {
+    typedef P3Shape<real, N, V> S;
+    typedef typename CT<real>::t cplx;
+    static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
+        dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
+        k_p3_z_cross<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare() { return set_smem(k_p3_z_cross<real, N, S::L, S::T, S::R3>, S::smem); }
+};
+
+template <typename real, int N> struct MiscLaunch {
+    typedef ZShape<real, N> Z;
+    typedef typename CT<real>::t cplx;
+    template <typename ioreal>
+    static cudaError_t zfwd(const Geo &g, const void *tw, const void *u, void *B, cudaStream_t st) {
+        dim3 grid((unsigned)((long long)N * N / Z::LZ));
+        k_zfwd_real<real, ioreal, N, Z::LZ, Z::T, Z::R><<<grid, Z::T, Z::smem, st>>>(g, (const cplx *)tw,
+                                                                                   (const ioreal *)u, (cplx *)B);
+        return cudaGetLastError();
+    }
+    template <typename ioreal> static cudaError_t prepare() {
+        return set_smem(k_zfwd_real<real, ioreal, N, Z::LZ, Z::T, Z::R>, Z::smem);
     }
     static cudaError_t curl(const Geo &g, const void *U, void *Om, cudaStream_t st) {
         const long long n = g.sS * g.nb;
         k_curl<real><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, (const cplx *)U, (cplx *)Om);
-        return cudaGetLastError();
-    }
-    static cudaError_t p5a(const Geo &g, const void *tw, const void *A, void *Nh, cudaStream_t st) {
-        auto k = k_p5a_xfwd<real, N, S::W, S::T, S::RC>;
-        dim3 grid(3 * g.nb, cdiv(g.Kz, S::W), g.Kx);
-        k<<<grid, S::T, S::smem_col, st>>>(g, (const cplx *)tw, (const cplx *)A, (cplx *)Nh);
-        return cudaGetLastError();
-    }
-    static cudaError_t p2(const Geo &g, const void *tw, const void *A, void *B, cudaStream_t st) {
-        auto k = k_p2_yinv<real, N, S::W, S::T, S::RC>;
-        dim3 grid(cdiv(g.Kz, S::W), N, 6 * g.nb);
-        k<<<grid, S::T, S::smem_col, st>>>(g, (const cplx *)tw, (const cplx *)A, (cplx *)B);
-        return cudaGetLastError();
-    }
-    static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
-        auto k = k_p3_z_cross<real, N, S::L3, S::T3, S::R3>;
-        dim3 grid((unsigned)((long long)N * N / S::L3 * g.nb));
-        k<<<grid, S::T3, S::smem_p3, st>>>(g, (const cplx *)tw, (cplx *)B);
-        return cudaGetLastError();
-    }
-    static cudaError_t p4(const Geo &g, const void *tw, const void *B, void *A, cudaStream_t st) {
-        auto k = k_p4_yfwd<real, N, S::W, S::T, S::RC>;
-        dim3 grid(cdiv(g.Kz, S::W), N, 3 * g.nb);
-        k<<<grid, S::T, S::smem_col, st>>>(g, (const cplx *)tw, (const cplx *)B, (cplx *)A);
-        return cudaGetLastError();
-    }
-    template <typename ioreal>
-    static cudaError_t zfwd(const Geo &g, const void *tw, const void *u, void *B, cudaStream_t st) {
-        auto k = k_zfwd_real<real, ioreal, N, S::LZ, S::TZ, S::R3>;
-        dim3 grid((unsigned)((long long)N * N / S::LZ));
-        k<<<grid, S::TZ, S::smem_zf, st>>>(g, (const cplx *)tw, (const ioreal *)u, (cplx *)B);
         return cudaGetLastError();
     }
 };
@@ -106,6 +178,8 @@ template <typename real, typename acc> struct UpdLaunch {
         a.adt = e.adt;
         a.bdt = e.bdt;
         a.stage = e.stage;
+        a.dt = e.dt;
+        a.ifrk = e.ifrk;
         const long long n = g.sS * g.nb;
         const unsigned blocks = (unsigned)((n + 255) / 256);
         k_p5b_update<real, acc><<<blocks, 256, 0, st>>>(g, (const cplx *)Nh, a);
@@ -113,53 +187,61 @@ template <typename real, typename acc> struct UpdLaunch {
     }
 };
 
-// Raise the dynamic shared-memory limit of every kernel of one (N, dtype);
-// called once at handle creation, outside any stream capture.
-template <typename real, typename ioreal, int N> cudaError_t prepare_all() {
-    typedef Shape<real, N> S;
-    cudaError_t e;
-    if ((e = set_smem(k_p1_xinv<real, N, S::W, S::T, S::RC>, S::smem_col)) != cudaSuccess) return e;
-    if ((e = set_smem(k_p2_yinv<real, N, S::W, S::T, S::RC>, S::smem_col)) != cudaSuccess) return e;
-    if ((e = set_smem(k_p3_z_cross<real, N, S::L3, S::T3, S::R3>, S::smem_p3)) != cudaSuccess) return e;
-    if ((e = set_smem(k_p4_yfwd<real, N, S::W, S::T, S::RC>, S::smem_col)) != cudaSuccess) return e;
-    if ((e = set_smem(k_zfwd_real<real, ioreal, N, S::LZ, S::TZ, S::R3>, S::smem_zf)) != cudaSuccess) return e;
-    return set_smem(k_p5a_xfwd<real, N, S::W, S::T, S::RC>, S::smem_col);
+// ------------------------------------------------------------------ tables
+template <typename real, int N, int V> static void fill_col(PassSet *ps) {
+    if constexpr (V < PassSet::NCOLV) {
+        typedef ColShape<real, N, V> S;
+        if constexpr (S::valid) {
+            ps->p1[V] = ColLaunch<real, N, V>::p1;
+            ps->p2[V] = ColLaunch<real, N, V>::p2;
+            ps->p4[V] = ColLaunch<real, N, V>::p4;
+            ps->p5a[V] = ColLaunch<real, N, V>::p5a;
+            ps->prep_col[V] = ColLaunch<real, N, V>::prepare;
+            ps->col_w[V] = S::W;
+            ps->col_r[V] = S::RC;
+            ps->col_t[V] = S::T;
+        }
+        fill_col<real, N, V + 1>(ps);
+    }
+}
+
+template <typename real, int N, int V> static void fill_p3(PassSet *ps) {
+    if constexpr (V < PassSet::NP3V) {
+        typedef P3Shape<real, N, V> S;
+        if constexpr (S::valid) {
+            ps->p3[V] = P3Launch<real, N, V>::p3;
+            ps->prep_p3[V] = P3Launch<real, N, V>::prepare;
+            ps->p3_l[V] = S::L;
+            ps->p3_r[V] = S::R3;
+            ps->p3_t[V] = S::T;
+        }
+        fill_p3<real, N, V + 1>(ps);
+    }
 }
 
 template <int N> bool fill_passes(int dtype, PassSet *ps) {
+    *ps = PassSet();
     if (dtype == 1) {
-        typedef Shape<double, N> S;
-        ps->W = S::W; ps->T = S::T; ps->L3 = S::L3; ps->T3 = S::T3;
-        ps->smem_col = S::smem_col; ps->smem_p3 = S::smem_p3;
-        ps->p1 = ColLaunch<double, N>::p1;
-        ps->curl = ColLaunch<double, N>::curl;
-        ps->p2 = ColLaunch<double, N>::p2;
-        ps->p3 = ColLaunch<double, N>::p3;
-        ps->p4 = ColLaunch<double, N>::p4;
-        ps->p5a = ColLaunch<double, N>::p5a;
+        fill_col<double, N, 0>(ps);
+        fill_p3<double, N, 0>(ps);
+        ps->curl = MiscLaunch<double, N>::curl;
         ps->p5b = UpdLaunch<double, double>::p5b;
-        ps->zfwd = ColLaunch<double, N>::template zfwd<double>;
-        ps->prepare = prepare_all<double, double, N>;
+        ps->zfwd = MiscLaunch<double, N>::template zfwd<double>;
+        ps->prep_misc = MiscLaunch<double, N>::template prepare<double>;
         return true;
     }
     if (dtype == 0 || dtype == 2) {
-        typedef Shape<float, N> S;
-        ps->W = S::W; ps->T = S::T; ps->L3 = S::L3; ps->T3 = S::T3;
-        ps->smem_col = S::smem_col; ps->smem_p3 = S::smem_p3;
-        ps->p1 = ColLaunch<float, N>::p1;
-        ps->curl = ColLaunch<float, N>::curl;
-        ps->p2 = ColLaunch<float, N>::p2;
-        ps->p3 = ColLaunch<float, N>::p3;
-        ps->p4 = ColLaunch<float, N>::p4;
-        ps->p5a = ColLaunch<float, N>::p5a;
+        fill_col<float, N, 0>(ps);
+        fill_p3<float, N, 0>(ps);
+        ps->curl = MiscLaunch<float, N>::curl;
         if (dtype == 0) {
             ps->p5b = UpdLaunch<float, float>::p5b;
-            ps->zfwd = ColLaunch<float, N>::template zfwd<float>;
-            ps->prepare = prepare_all<float, float, N>;
+            ps->zfwd = MiscLaunch<float, N>::template zfwd<float>;
+            ps->prep_misc = MiscLaunch<float, N>::template prepare<float>;
         } else {
             ps->p5b = UpdLaunch<float, double>::p5b;
-            ps->zfwd = ColLaunch<float, N>::template zfwd<double>;
-            ps->prepare = prepare_all<float, double, N>;
+            ps->zfwd = MiscLaunch<float, N>::template zfwd<double>;
+            ps->prep_misc = MiscLaunch<float, N>::template prepare<double>;
         }
         return true;
     }

@@ -57,7 +57,9 @@ struct UpdateArgs {
     const double *nu_box;  // per-box viscosity (batched boxes), or nullptr for nu
     double adt;      // a_s * dt
     double bdt;      // b_s * dt
+    double dt;       // time step (integrating-factor scheme)
     int stage;
+    int ifrk;        // 1: integrating-factor RK4 (exact viscous factor), 0: classical RK4
 };
 
 __device__ __forceinline__ int compact_to_k(int i, int K) { return i <= K ? i : i - (2 * K + 1); }
@@ -369,6 +371,56 @@ __device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real,
     return next;
 }
 
+// Integrating-factor (Lawson) RK4 stage update, k = this stage's projected
+// nonlinear term (no viscous term):
+//   s = 0: u1 = E2 u0 + (dt/6) E2 k,   next = E1 (u0 + dt/2 k)
+//   s = 1: u1 += (dt/3) E1 k,          next = E1 u0 + dt/2 k
+//   s = 2: u1 += (dt/3) E1 k,          next = E2 u0 + dt E1 k
+//   s = 3: u1 += (dt/6) k  -> the new step-start state.
+template <typename real, typename acc>
+__device__ __forceinline__ typename CT<real>::t rk_update_if(const UpdateArgs<real, acc> &a, long long m, int comp,
+                                                             long long sS, typename CT<real>::t du, acc e1,
+                                                             acc e2) {
+    typedef typename CT<real>::t cplx;
+    typedef typename CT<acc>::t cacc;
+    const long long e = comp * sS + m;
+    const acc dx = (acc)du.x, dy = (acc)du.y, dt = (acc)a.dt;
+    cacc u0, u1;
+    if (a.stage < 3) u0 = a.U0[e];
+    if (a.stage > 0) u1 = a.U1[e];
+    cplx next;
+    if (a.stage == 0) {
+        const acc c = (dt / (acc)6) * e2;
+        u1.x = e2 * u0.x + c * dx;
+        u1.y = e2 * u0.y + c * dy;
+        next = cmk<cplx>((double)(e1 * (u0.x + (dt / (acc)2) * dx)), (double)(e1 * (u0.y + (dt / (acc)2) * dy)));
+    } else if (a.stage == 1) {
+        const acc c = (dt / (acc)3) * e1;
+        u1.x += c * dx;
+        u1.y += c * dy;
+        next = cmk<cplx>((double)(e1 * u0.x + (dt / (acc)2) * dx), (double)(e1 * u0.y + (dt / (acc)2) * dy));
+    } else if (a.stage == 2) {
+        const acc c = (dt / (acc)3) * e1;
+        u1.x += c * dx;
+        u1.y += c * dy;
+        const acc d = dt * e1;
+        next = cmk<cplx>((double)(e2 * u0.x + d * dx), (double)(e2 * u0.y + d * dy));
+    } else {
+        const acc c = dt / (acc)6;
+        u1.x += c * dx;
+        u1.y += c * dy;
+        next = cmk<cplx>((double)u1.x, (double)u1.y);
+    }
+    if (a.stage < 3) {
+        a.U1[e] = u1;
+        a.Uout[e] = next;
+    } else {
+        a.U0out[e] = u1;
+        if (a.Uout) a.Uout[e] = next;
+    }
+    return next;
+}
+
 // P5a: forward transform along x of the 3 fields, keep the Kx stored rows;
 // the result N^ (dealiased by construction) goes to a compact buffer.
 template <typename real, int N, int W, int T, int MAXR>
@@ -433,10 +485,22 @@ __global__ void k_p5b_update(Geo g, const typename CT<real>::t *__restrict__ Nh,
         const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
         const real dim = (kx * n0.y + ky * n1.y + kzr * n2.y) * inv;
         const cplx u0 = args.U[m], u1 = args.U[sS + m], u2 = args.U[2 * sS + m];
-        const real vk = nu * k2;
-        const cplx x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
-        const cplx x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
-        const cplx x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+        cplx x0, x1, x2;
+        if (args.ifrk && args.stage >= 0) {
+            // integrating factor: the stage value is the projected nonlinear term
+            // alone; the viscous decay enters through E1 = exp(-nu k^2 dt/2),
+            // E2 = exp(-nu k^2 dt), evaluated in the accumulator precision
+            const acc L = (acc)nu * (acc)k2;
+            const acc e1 = exp(-L * (acc)(0.5 * args.dt)), e2 = exp(-L * (acc)args.dt);
+            x0 = rk_update_if<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre, n0.y - kx * dim), e1, e2);
+            x1 = rk_update_if<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre, n1.y - ky * dim), e1, e2);
+            x2 = rk_update_if<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre, n2.y - kzr * dim), e1, e2);
+        } else {
+            const real vk = nu * k2;
+            x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
+            x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
+            x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+        }
         if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
             cplx ox, oy, oz;
             curl_mode<cplx, real>(kx, ky, kzr, x0, x1, x2, ox, oy, oz);

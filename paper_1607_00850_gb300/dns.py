@@ -42,6 +42,12 @@ SIGNATURES = {
     "dns_set_time": (_i, [_vp, _d, ctypes.c_long]),
     "dns_query": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i), _dp, _dp]),
     "dns_device_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong)]),
+    "dns_set_integrator": (_i, [_vp, _i]),
+    "dns_autotune": (_i, [_vp, ctypes.c_char_p, ctypes.POINTER(_i)]),
+    "dns_get_plan": (_i, [_vp, ctypes.POINTER(_i)]),
+    "dns_set_plan": (_i, [_vp, ctypes.POINTER(_i)]),
+    "dns_variant_info": (_i, [_vp, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "dns_ensemble_autotune": (_i, [_vp, ctypes.c_char_p]),
     "dns_ensemble_init": (_i, [_i, ctypes.POINTER(_i), _dp, _d, _i, _vp, ctypes.POINTER(_vp)]),
     "dns_ensemble_free": (_i, [_vp]),
     "dns_ensemble_set_velocity": (_i, [_vp, _i, _vp, _i]),
@@ -214,6 +220,47 @@ def dns_energy_noalloc(N: int, dtype: int, uhat, nu: float, out=None, stream: in
     _check(load().dns_energy_noalloc(int(N), int(dtype), p, float(nu), ctypes.cast(po, _dp), do, stream or None),
            "dns_energy_noalloc")
     return out
+
+
+DNS_RK4, DNS_IFRK4 = 0, 1
+
+
+def dns_set_integrator(h: int, kind: int) -> None:
+    _check(load().dns_set_integrator(h, int(kind)), "dns_set_integrator")
+
+
+PASSES = ("inverse x", "inverse y", "z + cross", "forward y", "forward x")
+
+
+def dns_autotune(h: int, cache_path: str | None = None) -> list:
+    plan = (ctypes.c_int * 5)()
+    _check(load().dns_autotune(h, cache_path.encode() if cache_path else None, plan), "dns_autotune")
+    return list(plan)
+
+
+def dns_get_plan(h: int) -> list:
+    plan = (ctypes.c_int * 5)()
+    _check(load().dns_get_plan(h, plan), "dns_get_plan")
+    return list(plan)
+
+
+def dns_set_plan(h: int, plan) -> None:
+    arr = (ctypes.c_int * 5)(*[int(p) for p in plan])
+    _check(load().dns_set_plan(h, arr), "dns_set_plan")
+
+
+def dns_variant_info(h: int, pass_: int, variant: int):
+    """(lines per block, radix cap, threads) of a compiled variant, or None."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    rc = load().dns_variant_info(h, int(pass_), int(variant), ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc == 6:
+        return None
+    _check(rc, "dns_variant_info")
+    return a.value, b.value, c.value
+
+
+def dns_ensemble_autotune(e: int, cache_path: str | None = None) -> None:
+    _check(load().dns_ensemble_autotune(e, cache_path.encode() if cache_path else None), "dns_ensemble_autotune")
 
 
 def dns_ensemble_init(Ns, nus, dt: float, dtype: int = DNS_F32, stream: int | None = None) -> int:

@@ -310,3 +310,29 @@ def test_planted_mistakes_are_caught(mutant):
     import oracle
     o = oracle.load_mutant(mutant)
     assert _battery(o), f"mutant {mutant} passed every pin"
+
+
+# ---------------------------------------------------------------- integrating-factor RK4
+
+@pytest.mark.parametrize("kf,dt", [(1, 0.1), (2, 0.3), (3, 2.0)])
+def test_if_rk4_decay_is_exact_even_when_classical_rk4_is_unstable(orc, kf, dt):
+    # ABC flows have no nonlinear term, so the integrating factor makes the
+    # step exact: uhat_n = exp(-nu kf^2 n dt) uhat_0 for any dt
+    N, nu, n = 12, 0.5, 4
+    uh = inputs.abc_flow(N, kf=kf)
+    got = orc.rk4_if(uh, nu, dt, n)
+    assert np.abs(got - np.exp(-nu * kf * kf * n * dt) * uh).max() < 1e-13 * np.abs(uh).max()
+    z = -nu * kf * kf * dt
+    if z < -2.8:  # outside classical RK4's real stability interval
+        assert abs(1 + z + z * z / 2 + z ** 3 / 6 + z ** 4 / 24) > 1
+
+
+def test_if_rk4_is_fourth_order_and_agrees_with_rk4(orc):
+    N, nu, T = 16, 0.05, 0.4
+    uh = inputs.taylor_green(N)
+    ref = orc.rk4_if(uh, nu, T / 32, 32)
+    e1 = np.abs(orc.rk4_if(uh, nu, T / 4, 4) - ref).max()
+    e2 = np.abs(orc.rk4_if(uh, nu, T / 8, 8) - ref).max()
+    assert 12.0 < e1 / e2 < 20.0
+    # both integrators converge to the same solution of Eq. NSfinal
+    assert np.abs(orc.rk4(uh, nu, T / 32, 32) - ref).max() < 1e-6 * np.abs(uh).max()
