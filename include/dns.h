@@ -188,6 +188,61 @@ int dns_ensemble_time(dns_ensemble e, double *t, long *step);
 int dns_ensemble_autotune(dns_ensemble e, const char *cache_path);
 
 /* ------------------------------------------------------------------------
+ * Learned subgrid closure for a coarse LES (not in the paper).  The LES
+ * solves the filtered equations: Eq. NSfinal on the sharp-cutoff filtered
+ * field ubar (|k_i| <= kc = floor((n-1)/3) on an n^3 mesh) plus the term
+ * P[ m (-i k_j tau_ij^) ] with tau_ij = filt(u_i u_j) - ubar_i ubar_j.  A
+ * network maps the 9 filtered velocity gradients g[3i+j] = d_j ubar_i to the
+ * 6 stresses (order xx, yy, zz, xy, xz, yz): three periodic 3x3x3
+ * convolutions (cross-correlation; tap t = 9 tx + 3 ty + tz at offset
+ * (tx-1, ty-1, tz-1)), 9 -> 32 -> 32 -> 6 channels, GELU between them, BF16
+ * weights and activations on the tensor cores with FP32 accumulation, FP32
+ * master weights trained by Adam on the mean squared error.
+ * Physical fields are channel-major float arrays [C][n][n][n] in device
+ * memory.  n: 16, 32, 64, 128 or 256 for the closure and the data builder.
+ * One host thread and one stream per object; a network attached to an LES
+ * handle must not be trained or evaluated concurrently with its steps.
+ * ------------------------------------------------------------------------ */
+typedef struct dns_net_ctx *dns_net;
+typedef struct dns_les_builder_ctx *dns_les_builder;
+
+/* Network for an n^3 mesh, weights drawn from `seed` (scaled normal, zero
+ * biases).  cuda_stream as in dns_init. */
+int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *out);
+int dns_net_free(dns_net net);
+/* Number of FP32 parameters, in the order w1[32][9][27], b1[32],
+ * w2[32][32][27], b2[32], w3[6][32][27], b3[6]. */
+long dns_net_param_count(void);
+int dns_net_get_params(dns_net net, float *host, long count);
+int dns_net_set_params(dns_net net, const float *host, long count);
+/* Scales used only when the network serves as an LES closure: the network
+ * sees g * in_scale and the closure uses tau = output * out_scale (the
+ * normalisation the training data had).  Defaults 1, 1. */
+int dns_net_set_closure_scaling(dns_net net, double in_scale, double out_scale);
+/* tau[6][n^3] = network(g[9][n^3]) (device buffers; synchronising). */
+int dns_net_forward(dns_net net, const float *g, float *tau);
+/* Mean squared error loss of one sample and (optional) its gradient with
+ * respect to every parameter, in the parameter order above (host buffer). */
+int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count);
+/* One Adam step (beta 0.9, 0.999, eps 1e-8) on the mean gradient of
+ * nsamples consecutive samples g[s][9][n^3], tau[s][6][n^3]; loss = their
+ * mean loss before the step. */
+int dns_net_train_step(dns_net net, int nsamples, const float *g, const float *tau, double lr, double *loss);
+
+/* Training data from a DNS handle (DNS_F32, mesh N) for an n^3 LES:
+ * g[9][n^3] and tau[6][n^3] at the LES grid points, and (optional) the
+ * filtered field on the n mesh in the full spectral layout (complex64). */
+int dns_les_builder_create(int N, int n, dns_les_builder *out);
+int dns_les_builder_free(dns_les_builder b);
+int dns_les_builder_run(dns_les_builder b, dns_handle dns, float *g, float *tau, void *ubar_hat);
+
+/* Attach a network as the subgrid closure of an LES handle (DNS_F32, N =
+ * the network's n), or detach it with net = NULL.  With a closure attached,
+ * dns_step and dns_rhs add the closure term, evaluated from each stage's
+ * input.  The handle does not own the network. */
+int dns_les_set_closure(dns_handle h, dns_net net);
+
+/* ------------------------------------------------------------------------
  * Diagnostics without allocation.  The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc where they need the
  * numbers, such as code running while a stream is captured into a CUDA

@@ -56,6 +56,8 @@ struct dns_ctx {
     long long bytes = 0;
     int plan[5] = {0, 0, 0, 0, 0};  // variant of P1, P2, P3, P4, P5a
     int integrator = 0;             // DNS_RK4 or DNS_IFRK4
+    dns::LesClosure *closure = nullptr;  // learned subgrid closure (LES handles), or nullptr
+    void *Fext = nullptr;                // its forcing on the stored modes
 };
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -83,6 +85,8 @@ static void release(dns_ctx *h) {
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->host) cudaFreeHost(h->host);
+    if (h->closure) dns::les_closure_release(h->closure);
+    if (h->Fext) cudaFree(h->Fext);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -168,6 +172,7 @@ static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
     a.U0out = (s == 3) ? h->U0 : nullptr;
     a.dU = nullptr;
     a.Om = h->Om;
+    a.Fext = h->closure ? h->Fext : nullptr;
     a.nu = h->nu;
     a.nu_box = h->nu_box;
     a.adt = RK_A[s] * h->dt;
@@ -189,6 +194,9 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
     for (int s = 0; s < 4; ++s) {
         dns::UpdateArgsErased a = stage_args(h, s);
+        if (h->closure) {  // subgrid forcing from this stage's input
+            if ((e = dns::les_closure_forcing(h->closure, h->g, a.U, h->Fext, h->stream)) != cudaSuccess) return e;
+        }
         if ((e = h->ps.p1[h->plan[0]](h->g, h->tw, a.U, h->Om, h->A, scale, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
         if ((e = h->ps.p2[h->plan[1]](h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
@@ -466,6 +474,10 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
     a.dU = h->rout;
     a.nu = h->nu;
     a.stage = -1;
+    if (h->closure) {
+        CK(dns::les_closure_forcing(h->closure, h->g, h->rin, h->Fext, h->stream));
+        a.Fext = h->Fext;
+    }
     CK(h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream));
     CK(h->ps.p5b(h->g, h->B, a, h->stream));
     if (on_device) {
@@ -963,3 +975,35 @@ int dns_ensemble_autotune(dns_ensemble e, const char *cache_path) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- internal accessors (LES unit)
+namespace dns {
+int internal_view(dns_handle h, InternalView *v) {
+    if (!h || !v) return DNS_ERR_ARG;
+    v->N = h->N;
+    v->dtype = h->dtype;
+    v->g = h->g;
+    v->U0 = h->U0;
+    v->stream = h->stream;
+    return DNS_OK;
+}
+
+int internal_set_closure(dns_handle h, LesClosure *c) {
+    if (!h) return DNS_ERR_ARG;
+    if (h->closure) les_closure_release(h->closure);
+    h->closure = c;
+    if (c && !h->Fext) {
+        if (cudaMalloc(&h->Fext, 3 * h->g.sS * h->creal) != cudaSuccess) {
+            h->Fext = nullptr;
+            h->closure = nullptr;
+            les_closure_release(c);
+            return DNS_ERR_OOM;
+        }
+    }
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    return DNS_OK;
+}
+}  // namespace dns

@@ -13,6 +13,7 @@ struct UpdateArgsErased {
     const void *U, *U0;
     void *U1, *Uout, *U0out, *dU;
     void *Om;  // curl of the next stage input out, or nullptr
+    const void *Fext;  // forcing added to the nonlinear term before the projection, or nullptr
     double nu, adt, bdt, dt;
     const double *nu_box;  // per-box viscosity for batched boxes, or nullptr
     int stage;  // 0..3 RK4 stage, -1 right-hand side only, -2 raw forward transform
@@ -29,7 +30,7 @@ typedef cudaError_t (*Prep)();
 // (nullptr where a shape is not compiled) and the untuned kernels.
 struct PassSet {
     static constexpr int NCOLV = 3;  // column-pass variants (W, RC)
-    static constexpr int NP3V = 4;   // z-pass variants (L, R3)
+    static constexpr int NP3V = 6;   // z-pass variants (L, R3)
     ColP1 p1[NCOLV] = {};
     ColPass p2[NCOLV] = {}, p4[NCOLV] = {}, p5a[NCOLV] = {};
     Prep prep_col[NCOLV] = {};
@@ -47,5 +48,28 @@ struct PassSet {
 
 // dtype: 0 = F32, 1 = F64, 2 = F32_ACC64.
 typedef bool (*PassGetter)(int dtype, PassSet *out);
+
+// Learned-closure hook of an LES handle (implemented in dns_les.cu): from the
+// stage input U (compact, FP32, one box) compute the forcing -i k_j tau_ij^
+// on the stored modes into Fext (compact, 3 fields), on `stream`.
+struct LesClosure;
+cudaError_t les_closure_forcing(LesClosure *c, const Geo &g, const void *U, void *Fext, cudaStream_t stream);
+void les_closure_release(LesClosure *c);
+}  // namespace dns
+
+#include "dns.h"
+#include "dns_passes.cuh"
+
+namespace dns {
+// What the LES unit needs to see of a handle (defined in dns_api.cu).
+struct InternalView {
+    int N, dtype;
+    Geo g;
+    const void *U0;
+    cudaStream_t stream;
+};
+int internal_view(dns_handle h, InternalView *v);
+// Attach (or, with nullptr, detach) a closure; the handle takes ownership.
+int internal_set_closure(dns_handle h, LesClosure *c);
 
 }  // namespace dns

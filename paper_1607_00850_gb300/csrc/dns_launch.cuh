@@ -20,19 +20,23 @@ namespace dns {
 constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename real> struct VariantTable;
+// P3 variants: lines per block lmax >> p3S (lmax = the most lines that fit
+// 512 threads), radix cap p3R, blocks the compiler keeps resident p3M.
 template <> struct VariantTable<float> {
     static constexpr int BUD = 32;
     static constexpr int colW[3] = {16, 32, 16};
     static constexpr int colR[3] = {16, 16, 8};
-    static constexpr int p3L[4] = {8, 4, 16, 8};
-    static constexpr int p3R[4] = {32, 32, 32, 16};
+    static constexpr int p3S[6] = {0, 0, 1, 1, 2, 0};
+    static constexpr int p3R[6] = {32, 32, 32, 32, 32, 16};
+    static constexpr int p3M[6] = {1, 2, 1, 2, 2, 1};
 };
 template <> struct VariantTable<double> {
     static constexpr int BUD = 16;
     static constexpr int colW[3] = {8, 16, 8};
     static constexpr int colR[3] = {8, 8, 16};
-    static constexpr int p3L[4] = {4, 2, 8, 4};
-    static constexpr int p3R[4] = {16, 16, 16, 8};
+    static constexpr int p3S[6] = {0, 0, 1, 1, 2, 0};
+    static constexpr int p3R[6] = {16, 16, 16, 16, 16, 8};
+    static constexpr int p3M[6] = {1, 2, 1, 2, 2, 1};
 };
 
 __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
@@ -56,22 +60,21 @@ __host__ __device__ constexpr int pow2_floor(int x) {
     return p;
 }
 
-// P3 keeps at most 512 threads per block (at least 128 registers each); the
-// default variant is clamped to that, the others are only compiled if their
-// L fits as asked.
+// P3 keeps at most 512 threads per block (at least 128 registers each) and
+// at most 16 lines; lmax is the largest such power of two dividing N.
 template <typename real, int N, int V> struct P3Shape {
     typedef VariantTable<real> VT;
     static constexpr int pow2 = (N & -N);  // largest power of two dividing N
-    static constexpr int lmax = pow2_floor(512 * VT::BUD / (3 * N)) < 1 ? 1 : pow2_floor(512 * VT::BUD / (3 * N));
-    static constexpr int Lreq = VT::p3L[V];
-    static constexpr int L0 = Lreq < pow2 ? Lreq : pow2;
-    static constexpr int L = (V == 0 && L0 > lmax) ? lmax : L0;
+    static constexpr int lfit = pow2_floor(512 * VT::BUD / (3 * N)) < 1 ? 1 : pow2_floor(512 * VT::BUD / (3 * N));
+    static constexpr int lmax = lfit < 16 ? (lfit < pow2 ? lfit : pow2) : (16 < pow2 ? 16 : pow2);
+    static constexpr int L = (lmax >> VT::p3S[V]) < 1 ? 1 : (lmax >> VT::p3S[V]);
     static constexpr int R3 = VT::p3R[V];
     static constexpr int T = at_least_32(raw_threads(N, 3 * L, VT::BUD));
     typedef typename CT<real>::t cplx;
     static constexpr size_t smem = sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
-    static constexpr bool valid =
-        (V == 0 || (N >= 64 && Lreq <= lmax && Lreq <= pow2)) && T <= 1024 && smem <= kMaxSmem;
+    static constexpr int MINB = VT::p3M[V];
+    static constexpr bool valid = (V == 0 || (N >= 64 && (lmax >> VT::p3S[V]) >= 1)) && T <= 1024 &&
+                                  smem <= kMaxSmem && (MINB == 1 || (2 * smem <= kMaxSmem && 2 * T <= 1024));
 };
 
 // physical-input z pass (column-mapped, not tuned)
@@ -135,10 +138,16 @@ template <typename real, int N, int V> struct P3Launch {
     typedef typename CT<real>::t cplx;
     static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
         dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
-        k_p3_z_cross<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
+        if constexpr (S::MINB == 2)
+            k_p3_z_cross_2b<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
+        else
+            k_p3_z_cross<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
         return cudaGetLastError();
     }
-    static cudaError_t prepare() { return set_smem(k_p3_z_cross<real, N, S::L, S::T, S::R3>, S::smem); }
+    static cudaError_t prepare() {
+        if constexpr (S::MINB == 2) return set_smem(k_p3_z_cross_2b<real, N, S::L, S::T, S::R3>, S::smem);
+        else return set_smem(k_p3_z_cross<real, N, S::L, S::T, S::R3>, S::smem);
+    }
 };
 
 template <typename real, int N> struct MiscLaunch {
@@ -173,6 +182,7 @@ template <typename real, typename acc> struct UpdLaunch {
         a.U0out = (cacc *)e.U0out;
         a.dU = (cacc *)e.dU;
         a.Om = (cplx *)e.Om;
+        a.Fext = (const cplx *)e.Fext;
         a.nu = e.nu;
         a.nu_box = e.nu_box;
         a.adt = e.adt;

@@ -1,0 +1,831 @@
+// Learned subgrid closure for a coarse LES (not in the paper): training data
+// from the DNS, a 3-layer periodic 3x3x3 convolutional network (9 filtered
+// velocity gradients -> 32 -> 32 -> 6 subgrid stresses, GELU, BF16 operands,
+// FP32 accumulation) trained with Adam, and the closure term in the LES
+// right-hand side.  C ABI in include/dns.h (dns_net_*, dns_les_*).
+//
+// Convolutions are implicit GEMMs on the tensor cores with mma.sync
+// m16n8k16 (BF16 in, FP32 accumulate): M = voxels, N = output channels,
+// K = 27 taps x input channels.  Activations are voxel-major [V][C] BF16 so a
+// tap's K slice is contiguous; weights are [Cout][27][Cin] BF16.  The input
+// gradient is the same convolution with flipped taps and transposed weights;
+// the weight gradient is a per-tap GEMM over voxel chunks (dY^T X_t) with
+// both operands transposed through shared memory, reduced over chunks in a
+// fixed order.
+#include "dns.h"
+#include "dns_internal.h"
+#include "dns_les.cuh"
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+namespace dns {
+namespace les {
+
+// ---------------------------------------------------------------- complex FFT launchers
+template <int N> struct C2C {
+    static constexpr int W = 16;
+    static constexpr int T = N * W / 16 < 32 ? 32 : (N * W / 16 > 1024 ? 1024 : N * W / 16);
+    static constexpr int L = 16;  // z lines per block
+    static constexpr int TZ = N * L / 16 < 32 ? 32 : (N * L / 16 > 1024 ? 1024 : N * L / 16);
+    static constexpr size_t smem_col = sizeof(float2) * (N + N * W);
+    static constexpr size_t smem_row = sizeof(float2) * (N + L * row_ld(N));
+    template <int SIGN> static cudaError_t run(float2 *a, const float2 *tw, int nfield, cudaStream_t st) {
+        static_assert(N % L == 0 || N < L, "lines");
+        cudaError_t e;
+        auto kx = k_c2c_axis<N, W, T, SIGN, 0>;
+        auto ky = k_c2c_axis<N, W, T, SIGN, 1>;
+        auto kz = k_c2c_axis<N, L, TZ, SIGN, 2>;
+        if ((e = cudaFuncSetAttribute(kx, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(ky, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_col)) != cudaSuccess) return e;
+        if ((e = cudaFuncSetAttribute(kz, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_row)) != cudaSuccess) return e;
+        const dim3 gc(N / W, N, nfield);
+        kx<<<gc, T, smem_col, st>>>(a, tw);
+        ky<<<gc, T, smem_col, st>>>(a, tw);
+        kz<<<(unsigned)((long long)N * N * nfield / L), TZ, smem_row, st>>>(a, tw);
+        return cudaGetLastError();
+    }
+};
+
+static cudaError_t c2c(int N, float2 *a, const float2 *tw, int nfield, int sign, cudaStream_t st) {
+    switch (N) {
+#define DNS_C2C(n) \
+    case n: return sign < 0 ? C2C<n>::run<-1>(a, tw, nfield, st) : C2C<n>::run<+1>(a, tw, nfield, st);
+        DNS_C2C(16) DNS_C2C(32) DNS_C2C(64) DNS_C2C(128) DNS_C2C(256)
+#undef DNS_C2C
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+static bool c2c_supported(int N) { return N == 16 || N == 32 || N == 64 || N == 128 || N == 256; }
+
+static inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------- network kernels
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_d(float x) {
+    return 0.5f * (1.0f + erff(x * 0.70710678118654752f)) + x * 0.39894228040143268f * expf(-0.5f * x * x);
+}
+
+__device__ __forceinline__ uint32_t ld_b32(const __nv_bfloat16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
+
+__device__ __forceinline__ void mma_bf16(float *d, uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t b0,
+                                         uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ long long nbr(int n, int x, int y, int z, int t) {
+    const int dx = t / 9 - 1, dy = (t / 3) % 3 - 1, dz = t % 3 - 1;
+    x = (x + dx + n) % n;
+    y = (y + dy + n) % n;
+    z = (z + dz + n) % n;
+    return ((long long)x * n + y) * n + z;
+}
+
+enum { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DGRAD = 2 };
+
+// Y[v][o] = b[o] + sum_{t,c} X[v + off(t)][c] W[o][t][c], one warp per 16
+// voxels along z, all COUT outputs.  Epilogues:
+//   EPI_HIDDEN: Z = Y (float) and A = bf16(gelu(Z));  EPI_OUT: Z = Y;
+//   EPI_DGRAD:  A = bf16(Y * gelu'(Zp)) (Y is dL/da of the layer below).
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(128) k_conv(int n, const __nv_bfloat16 *__restrict__ X,
+                                              const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
+                                              float *__restrict__ Z, __nv_bfloat16 *__restrict__ A,
+                                              const float *__restrict__ Zp) {
+    constexpr int NT = COUT / 8;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
+    const long long v0 = ((long long)blockIdx.x * 4 + warp) * 16;  // 16 voxels along z
+    const long long V = (long long)n * n * n;
+    if (v0 >= V) return;
+    const int z0 = (int)(v0 % n), y = (int)((v0 / n) % n), x = (int)(v0 / ((long long)n * n));
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int t = 0; t < 27; ++t) {
+        const long long r0 = nbr(n, x, y, z0 + g, t), r1 = nbr(n, x, y, z0 + g + 8, t);
+        const __nv_bfloat16 *xa = X + r0 * CIN, *xb = X + r1 * CIN;
+#pragma unroll
+        for (int kc = 0; kc < CIN; kc += 16) {
+            const uint32_t a0 = ld_b32(xa + kc + 2 * tg), a1 = ld_b32(xb + kc + 2 * tg);
+            const uint32_t a2 = ld_b32(xa + kc + 8 + 2 * tg), a3 = ld_b32(xb + kc + 8 + 2 * tg);
+#pragma unroll
+            for (int j = 0; j < NT; ++j) {
+                const __nv_bfloat16 *w = W + ((long long)(j * 8 + g) * 27 + t) * CIN + kc + 2 * tg;
+                mma_bf16(acc[j], a0, a1, a2, a3, ld_b32(w), ld_b32(w + 8));
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const long long v = v0 + g + 8 * h;
+            const int o = j * 8 + 2 * tg;
+            float y0 = acc[j][2 * h], y1 = acc[j][2 * h + 1];
+            if (bias) {
+                y0 += bias[o];
+                y1 += bias[o + 1];
+            }
+            if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
+                Z[v * COUT + o] = y0;
+                Z[v * COUT + o + 1] = y1;
+            }
+            if constexpr (EPI == EPI_HIDDEN) {
+                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(gelu_f(y0), gelu_f(y1));
+            }
+            if constexpr (EPI == EPI_DGRAD) {
+                const float d0 = y0 * gelu_d(Zp[v * COUT + o]), d1 = y1 * gelu_d(Zp[v * COUT + o + 1]);
+                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(d0, d1);
+            }
+        }
+    }
+}
+
+// Weight gradient partials: block (chunk, tap) accumulates
+// D[o][c] = sum_{v in chunk} dY[v][o] X[v + off(t)][c] (M = COUTP rows o,
+// N = CIN cols c, K = voxels) and writes it to P[chunk][t][o][c].  COUTP is
+// COUT rounded up to 16 (the MMA's M); the extra rows are zero.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(256) k_wgrad(int n, const __nv_bfloat16 *__restrict__ dY,
+                                               const __nv_bfloat16 *__restrict__ X, float *__restrict__ P,
+                                               int chunk) {
+    constexpr int COUTP = COUT < 16 ? 16 : COUT;
+    constexpr int MT = COUTP / 16, NT = CIN / 8;
+    constexpr int SUB = 128;  // voxels staged per round
+    constexpr int LDA = SUB + 8, LDB = SUB + 8;  // padded rows (bank spread)
+    __shared__ __align__(16) __nv_bfloat16 sA[COUTP * LDA];
+    __shared__ __align__(16) __nv_bfloat16 sB[CIN * LDB];
+    const int t = blockIdx.y;
+    const long long V = (long long)n * n * n;
+    const long long vbeg = (long long)blockIdx.x * chunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, tg = lane & 3;
+    // warps own (m-tile, n-tile) pairs round robin
+    constexpr int TILES = MT * NT;
+    float acc[(TILES + 7) / 8][4];
+#pragma unroll
+    for (int i = 0; i < (TILES + 7) / 8; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    for (long long vs = vbeg; vs < vbeg + chunk && vs < V; vs += SUB) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < SUB * COUTP; e += blockDim.x) {
+            const int v = e / COUTP, o = e % COUTP;
+            const long long vv = vs + v;
+            sA[o * LDA + v] = (o < COUT && vv < V) ? dY[vv * COUT + o] : __float2bfloat16(0.f);
+        }
+        for (int e = threadIdx.x; e < SUB * CIN; e += blockDim.x) {
+            const int v = e / CIN, c = e % CIN;
+            const long long vv = vs + v;
+            __nv_bfloat16 val = __float2bfloat16(0.f);
+            if (vv < V) {
+                const int z = (int)(vv % n), y = (int)((vv / n) % n), x = (int)(vv / ((long long)n * n));
+                val = X[nbr(n, x, y, z, t) * CIN + c];
+            }
+            sB[c * LDB + v] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < (TILES + 7) / 8; ++i) {
+            const int tile = warp + 8 * i;
+            if (tile < TILES) {
+                const int mt = tile / NT, nt = tile % NT;
+                for (int k = 0; k < SUB; k += 16) {
+                    const __nv_bfloat16 *a = sA + (mt * 16 + g) * LDA + k + 2 * tg;
+                    const __nv_bfloat16 *b = sB + (nt * 8 + g) * LDB + k + 2 * tg;
+                    mma_bf16(acc[i], ld_b32(a), ld_b32(a + 8 * LDA), ld_b32(a + 8), ld_b32(a + 8 * LDA + 8),
+                             ld_b32(b), ld_b32(b + 8));
+                }
+            }
+        }
+    }
+    float *out = P + ((long long)blockIdx.x * 27 + t) * COUT * CIN;
+#pragma unroll
+    for (int i = 0; i < (TILES + 7) / 8; ++i) {
+        const int tile = warp + 8 * i;
+        if (tile < TILES) {
+            const int mt = tile / NT, nt = tile % NT;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int o = mt * 16 + g + 8 * h, c = nt * 8 + 2 * tg;
+                if (o < COUT) {
+                    out[o * CIN + c] = acc[i][2 * h];
+                    out[o * CIN + c + 1] = acc[i][2 * h + 1];
+                }
+            }
+        }
+    }
+}
+
+// sum over chunks in a fixed order: G[o][t][c] (GPU layout) += sum_b P[b][t][o][c]
+__global__ void k_wgrad_reduce(const float *__restrict__ P, int nchunk, int cout, int cin, float *__restrict__ G) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int total = 27 * cout * cin;
+    if (e >= total) return;
+    const int t = e / (cout * cin), o = (e / cin) % cout, c = e % cin;
+    float s = 0.f;
+    for (int b = 0; b < nchunk; ++b) s += P[((long long)b * 27 + t) * cout * cin + o * cin + c];
+    G[((long long)o * 27 + t) * cin + c] += s;
+}
+
+// column sums of a [V][C] BF16 array into G (bias gradient), fixed order
+__global__ void k_colsum(const __nv_bfloat16 *__restrict__ d, long long V, int C, int creal, float *__restrict__ G) {
+    __shared__ float red[256];
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (long long v = threadIdx.x; v < V; v += blockDim.x) s += __bfloat162float(d[v * C + c]);
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && c < creal) G[c] += red[0];
+}
+
+// g[9][V] floats -> X0[V][16] BF16 (channels 9..15 zero)
+__global__ void k_prep_input(const float *__restrict__ g, long long V, __nv_bfloat16 *__restrict__ X0) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= V * 16) return;
+    const long long v = e / 16;
+    const int c = (int)(e % 16);
+    X0[e] = __float2bfloat16(c < 9 ? g[c * V + v] : 0.f);
+}
+
+// The output layer is computed 16 channels wide (the MMA's K granularity for
+// its input gradient); channels 6..15 are zero.
+constexpr int OUTP = 16;
+
+// MSE: dY[v][o] = 2 (Y - tau) / (6 V) (BF16, o < 6; padding zero), per-block partial loss
+__global__ void k_mse(const float *__restrict__ Y, const float *__restrict__ tau, long long V,
+                      __nv_bfloat16 *__restrict__ dY, double *__restrict__ partial) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        for (int o = 0; o < OUTP; ++o) {
+            float d = 0.f;
+            if (o < 6) {
+                d = Y[v * OUTP + o] - tau[o * V + v];
+                s += (double)d * d;
+            }
+            dY[v * OUTP + o] = __float2bfloat16(2.0f * d / (6.0f * (float)V));
+        }
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = red[0];
+}
+
+__global__ void k_sum_d(const double *p, int n, double scale, double *out) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < n; ++i) s += p[i];
+        *out += s * scale;
+    }
+}
+
+// Y[V][OUTP] -> tau[6][V] floats
+__global__ void k_out_to_tau(const float *__restrict__ Y, long long V, float *__restrict__ tau, float scale) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= 6 * V) return;
+    const int o = (int)(e / V);
+    tau[e] = scale * Y[(e % V) * OUTP + o];
+}
+
+// Master FP32 parameters in the oracle's layout ([Cout][Cin][27] weights)
+// -> BF16 padded [Coutp][27][Cinp] and the flipped transpose used for input
+// gradients, Wf[c][t][o] = W[o][26 - t][c] (padded to [Cinp... as Cout of the
+// transposed convolution][27][Coutp]).
+__global__ void k_pack_weights(const float *__restrict__ w, int cout, int cin, int coutp, int cinp,
+                               __nv_bfloat16 *__restrict__ Wp, __nv_bfloat16 *__restrict__ Wf) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= coutp * 27 * cinp) return;
+    const int o = e / (27 * cinp), t = (e / cinp) % 27, c = e % cinp;
+    const float v = (o < cout && c < cin) ? w[((long long)o * cin + c) * 27 + t] : 0.f;
+    Wp[e] = __float2bfloat16(v);
+    if (Wf) Wf[((long long)c * 27 + (26 - t)) * coutp + o] = __float2bfloat16(v);
+}
+
+// Adam on the master parameters; gradients of weights come in the GPU layout
+// [Coutp][27][Cinp] (gw_layout = 1) or are flat (biases, gw_layout = 0).
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ gsrc, int count, int gw_layout, int cout, int cin, int cinp,
+                       float lr, float b1, float b2, float eps, float c1, float c2) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= count) return;
+    float gr;
+    if (gw_layout) {
+        const int o = e / (cin * 27), c = (e / 27) % cin, t = e % 27;
+        gr = gsrc[((long long)o * 27 + t) * cinp + c];
+    } else {
+        gr = gsrc[e];
+    }
+    const float mm = b1 * m[e] + (1.f - b1) * gr;
+    const float vv = b2 * v[e] + (1.f - b2) * gr * gr;
+    m[e] = mm;
+    v[e] = vv;
+    p[e] -= lr * (mm / c1) / (sqrtf(vv / c2) + eps);
+}
+
+}  // namespace les
+}  // namespace dns
+
+using namespace dns::les;
+
+// ---------------------------------------------------------------- network object
+struct dns_net_ctx {
+    int n = 0;  // mesh the buffers are sized for
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    // master parameters (oracle layout), Adam moments, gradients
+    float *p = nullptr, *m = nullptr, *v = nullptr;
+    float *gw1 = nullptr, *gw2 = nullptr, *gw3 = nullptr, *gb = nullptr;  // GPU-layout weight grads; bias grads
+    long step = 0;
+    // BF16 packed weights
+    __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2f = nullptr, *W3f = nullptr;
+    // activations for one sample
+    __nv_bfloat16 *X0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY3 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
+    float *Z1 = nullptr, *Z2 = nullptr, *Y3 = nullptr, *wpart = nullptr;
+    double *lpart = nullptr, *lsum = nullptr, *hostd = nullptr;
+    int nchunk = 0;
+    float in_scale = 1.f, out_scale = 1.f;  // closure use: input g * in_scale, tau = output * out_scale
+};
+
+// parameter blocks in the flat master vector
+static const long NET_W1 = 32L * 9 * 27, NET_B1 = 32, NET_W2 = 32L * 32 * 27, NET_B2 = 32, NET_W3 = 6L * 32 * 27,
+                  NET_B3 = 6;
+static const long OFF_W1 = 0, OFF_B1 = OFF_W1 + NET_W1, OFF_W2 = OFF_B1 + NET_B1, OFF_B2 = OFF_W2 + NET_W2,
+                  OFF_W3 = OFF_B2 + NET_B2, OFF_B3 = OFF_W3 + NET_W3, NET_PARAMS = OFF_B3 + NET_B3;
+
+static void net_release(dns_net_ctx *c) {
+    if (!c) return;
+    void *bufs[] = {c->p, c->m, c->v, c->gw1, c->gw2, c->gw3, c->gb, c->W1, c->W2, c->W3, c->W2f, c->W3f, c->X0,
+                    c->A1, c->A2, c->dY3, c->dZ2, c->dZ1, c->Z1, c->Z2, c->Y3, c->wpart, c->lpart, c->lsum};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    if (c->hostd) cudaFreeHost(c->hostd);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+static cudaError_t net_pack(dns_net_ctx *c) {
+    k_pack_weights<<<nblk(32 * 27 * 16), 256, 0, c->stream>>>(c->p + OFF_W1, 32, 9, 32, 16, c->W1, nullptr);
+    k_pack_weights<<<nblk(32 * 27 * 32), 256, 0, c->stream>>>(c->p + OFF_W2, 32, 32, 32, 32, c->W2, c->W2f);
+    k_pack_weights<<<nblk(OUTP * 27 * 32), 256, 0, c->stream>>>(c->p + OFF_W3, 6, 32, OUTP, 32, c->W3, c->W3f);
+    return cudaGetLastError();
+}
+
+// forward of one sample already in X0; leaves Z1, A1, Z2, A2, Y3
+static cudaError_t net_forward_x0(dns_net_ctx *c, cudaStream_t st) {
+    const long long V = (long long)c->n * c->n * c->n;
+    const unsigned blocks = (unsigned)((V / 16 + 3) / 4);
+    k_conv<16, 32, EPI_HIDDEN><<<blocks, 128, 0, st>>>(c->n, c->X0, c->W1, c->p + OFF_B1, c->Z1, c->A1, nullptr);
+    k_conv<32, 32, EPI_HIDDEN><<<blocks, 128, 0, st>>>(c->n, c->A1, c->W2, c->p + OFF_B2, c->Z2, c->A2, nullptr);
+    k_conv<32, OUTP, EPI_OUT><<<blocks, 128, 0, st>>>(c->n, c->A2, c->W3, nullptr, c->Y3, nullptr, nullptr);
+    return cudaGetLastError();
+}
+
+__global__ void k_scale(float *g, int n, float s) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < n) g[e] *= s;
+}
+
+// the last layer's bias (6 entries) on its padded output
+__global__ void k_add_bias_out(float *Y, long long V, const float *b) {
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e < V * OUTP && (e % OUTP) < 6) Y[e] += b[e % OUTP];
+}
+
+static cudaError_t net_forward(dns_net_ctx *c, const float *g, cudaStream_t st) {
+    const long long V = (long long)c->n * c->n * c->n;
+    k_prep_input<<<nblk(V * 16), 256, 0, st>>>(g, V, c->X0);
+    cudaError_t e = net_forward_x0(c, st);
+    if (e != cudaSuccess) return e;
+    k_add_bias_out<<<nblk(V * OUTP), 256, 0, st>>>(c->Y3, V, c->p + OFF_B3);
+    return cudaGetLastError();
+}
+
+// backward of the sample in flight (after net_forward), accumulating gradients
+static cudaError_t net_backward(dns_net_ctx *c, const float *tau) {
+    const long long V = (long long)c->n * c->n * c->n;
+    const unsigned blocks = (unsigned)((V / 16 + 3) / 4);
+    const int lblocks = 256;
+    k_mse<<<lblocks, 256, 0, c->stream>>>(c->Y3, tau, V, c->dY3, c->lpart);
+    k_sum_d<<<1, 32, 0, c->stream>>>(c->lpart, lblocks, 1.0 / (6.0 * (double)V), c->lsum);
+    const dim3 wg(c->nchunk, 27);
+    // layer 3
+    k_wgrad<32, OUTP><<<wg, 256, 0, c->stream>>>(c->n, c->dY3, c->A2, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
+    k_wgrad_reduce<<<nblk(27 * OUTP * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, OUTP, 32, c->gw3);
+    k_colsum<<<OUTP, 256, 0, c->stream>>>(c->dY3, V, OUTP, 6, c->gb + 64);
+    k_conv<OUTP, 32, EPI_DGRAD><<<blocks, 128, 0, c->stream>>>(c->n, c->dY3, c->W3f, nullptr, nullptr, c->dZ2, c->Z2);
+    // layer 2
+    k_wgrad<32, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ2, c->A1, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
+    k_wgrad_reduce<<<nblk(27 * 32 * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, 32, 32, c->gw2);
+    k_colsum<<<32, 256, 0, c->stream>>>(c->dZ2, V, 32, 32, c->gb + 32);
+    k_conv<32, 32, EPI_DGRAD><<<blocks, 128, 0, c->stream>>>(c->n, c->dZ2, c->W2f, nullptr, nullptr, c->dZ1, c->Z1);
+    // layer 1
+    k_wgrad<16, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ1, c->X0, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
+    k_wgrad_reduce<<<nblk(27 * 32 * 16), 256, 0, c->stream>>>(c->wpart, c->nchunk, 32, 16, c->gw1);
+    k_colsum<<<32, 256, 0, c->stream>>>(c->dZ1, V, 32, 32, c->gb);
+    return cudaGetLastError();
+}
+
+#define NK(call)                       \
+    do {                               \
+        cudaError_t e_ = (call);       \
+        if (e_ != cudaSuccess) return DNS_ERR_CUDA; \
+    } while (0)
+
+extern "C" {
+
+int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *out) {
+    if (!out) return DNS_ERR_ARG;
+    *out = nullptr;
+    if (n < 16 || n > 256 || n % 16) return DNS_ERR_UNSUPPORTED;
+    dns_net_ctx *c = new (std::nothrow) dns_net_ctx();
+    if (!c) return DNS_ERR_OOM;
+    c->n = n;
+    const long long V = (long long)n * n * n;
+    c->nchunk = (int)((V + 2047) / 2048);
+    bool ok = true;
+    auto al = [&](void **p, size_t b) {
+        if (ok && cudaMalloc(p, b) != cudaSuccess) {
+            *p = nullptr;
+            ok = false;
+        }
+    };
+    al((void **)&c->p, sizeof(float) * NET_PARAMS);
+    al((void **)&c->m, sizeof(float) * NET_PARAMS);
+    al((void **)&c->v, sizeof(float) * NET_PARAMS);
+    al((void **)&c->gw1, sizeof(float) * 32 * 27 * 16);
+    al((void **)&c->gw2, sizeof(float) * 32 * 27 * 32);
+    al((void **)&c->gw3, sizeof(float) * OUTP * 27 * 32);
+    al((void **)&c->gb, sizeof(float) * 72);
+    al((void **)&c->W1, 2 * 32 * 27 * 16);
+    al((void **)&c->W2, 2 * 32 * 27 * 32);
+    al((void **)&c->W3, 2 * OUTP * 27 * 32);
+    al((void **)&c->W2f, 2 * 32 * 27 * 32);
+    al((void **)&c->W3f, 2 * 32 * 27 * OUTP);
+    al((void **)&c->X0, 2 * V * 16);
+    al((void **)&c->A1, 2 * V * 32);
+    al((void **)&c->A2, 2 * V * 32);
+    al((void **)&c->dY3, 2 * V * OUTP);
+    al((void **)&c->dZ2, 2 * V * 32);
+    al((void **)&c->dZ1, 2 * V * 32);
+    al((void **)&c->Z1, 4 * V * 32);
+    al((void **)&c->Z2, 4 * V * 32);
+    al((void **)&c->Y3, 4 * V * OUTP);
+    al((void **)&c->wpart, sizeof(float) * (size_t)c->nchunk * 27 * 32 * 32);
+    al((void **)&c->lpart, sizeof(double) * 256);
+    al((void **)&c->lsum, sizeof(double));
+    if (ok && cudaMallocHost((void **)&c->hostd, sizeof(double) * 4) != cudaSuccess) {
+        c->hostd = nullptr;
+        ok = false;
+    }
+    if (!ok) {
+        net_release(c);
+        return DNS_ERR_OOM;
+    }
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else if (cudaStreamCreate(&c->stream) != cudaSuccess) {
+        net_release(c);
+        return DNS_ERR_CUDA;
+    } else {
+        c->own_stream = true;
+    }
+    // He-style initialisation from a 64-bit LCG + Box-Muller on the host
+    std::vector<float> h(NET_PARAMS, 0.f);
+    unsigned long long s = seed * 6364136223846793005ULL + 1442695040888963407ULL;
+    auto unif = [&]() {
+        s = s * 6364136223846793005ULL + 1442695040888963407ULL;
+        return ((s >> 11) + 0.5) * (1.0 / 9007199254740992.0);
+    };
+    auto normal = [&]() { return std::sqrt(-2.0 * std::log(unif())) * std::cos(2.0 * M_PI * unif()); };
+    for (long i = 0; i < NET_W1; ++i) h[OFF_W1 + i] = (float)(normal() * std::sqrt(2.0 / (9 * 27)));
+    for (long i = 0; i < NET_W2; ++i) h[OFF_W2 + i] = (float)(normal() * std::sqrt(2.0 / (32 * 27)));
+    for (long i = 0; i < NET_W3; ++i) h[OFF_W3 + i] = (float)(normal() * std::sqrt(1.0 / (32 * 27)));
+    if (cudaMemcpy(c->p, h.data(), sizeof(float) * NET_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemset(c->m, 0, sizeof(float) * NET_PARAMS) != cudaSuccess ||
+        cudaMemset(c->v, 0, sizeof(float) * NET_PARAMS) != cudaSuccess || net_pack(c) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        net_release(c);
+        return DNS_ERR_CUDA;
+    }
+    *out = c;
+    return DNS_OK;
+}
+
+int dns_net_free(dns_net net) {
+    if (!net) return DNS_OK;
+    cudaStreamSynchronize(net->stream);
+    net_release(net);
+    return DNS_OK;
+}
+
+long dns_net_param_count(void) { return NET_PARAMS; }
+
+int dns_net_set_closure_scaling(dns_net net, double in_scale, double out_scale) {
+    if (!net || !(in_scale > 0.0) || !(out_scale > 0.0) || !std::isfinite(in_scale) || !std::isfinite(out_scale))
+        return DNS_ERR_ARG;
+    net->in_scale = (float)in_scale;
+    net->out_scale = (float)out_scale;
+    return DNS_OK;
+}
+
+int dns_net_get_params(dns_net net, float *host, long count) {
+    if (!net || !host || count != NET_PARAMS) return DNS_ERR_ARG;
+    NK(cudaMemcpyAsync(host, net->p, sizeof(float) * NET_PARAMS, cudaMemcpyDeviceToHost, net->stream));
+    NK(cudaStreamSynchronize(net->stream));
+    return DNS_OK;
+}
+
+int dns_net_set_params(dns_net net, const float *host, long count) {
+    if (!net || !host || count != NET_PARAMS) return DNS_ERR_ARG;
+    NK(cudaMemcpyAsync(net->p, host, sizeof(float) * NET_PARAMS, cudaMemcpyHostToDevice, net->stream));
+    NK(net_pack(net));
+    NK(cudaStreamSynchronize(net->stream));
+    return DNS_OK;
+}
+
+int dns_net_forward(dns_net net, const float *g, float *tau) {
+    if (!net || !g || !tau) return DNS_ERR_ARG;
+    const long long V = (long long)net->n * net->n * net->n;
+    NK(net_forward(net, g, net->stream));
+    k_out_to_tau<<<nblk(6 * V), 256, 0, net->stream>>>(net->Y3, V, tau, 1.0f);
+    NK(cudaGetLastError());
+    NK(cudaStreamSynchronize(net->stream));
+    return DNS_OK;
+}
+
+int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count) {
+    if (!net || !g || !tau || (grad_host && count != NET_PARAMS)) return DNS_ERR_ARG;
+    NK(cudaMemsetAsync(net->gw1, 0, sizeof(float) * 32 * 27 * 16, net->stream));
+    NK(cudaMemsetAsync(net->gw2, 0, sizeof(float) * 32 * 27 * 32, net->stream));
+    NK(cudaMemsetAsync(net->gw3, 0, sizeof(float) * OUTP * 27 * 32, net->stream));
+    NK(cudaMemsetAsync(net->gb, 0, sizeof(float) * 72, net->stream));
+    NK(cudaMemsetAsync(net->lsum, 0, sizeof(double), net->stream));
+    NK(net_forward(net, g, net->stream));
+    NK(net_backward(net, tau));
+    if (loss) {
+        NK(cudaMemcpyAsync(net->hostd, net->lsum, sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+    }
+    if (grad_host) {
+        // back to the master layout: weights [Cout][Cin][27], biases
+        std::vector<float> g1(32 * 27 * 16), g2(32 * 27 * 32), g3(OUTP * 27 * 32), gb(72);
+        NK(cudaMemcpyAsync(g1.data(), net->gw1, sizeof(float) * g1.size(), cudaMemcpyDeviceToHost, net->stream));
+        NK(cudaMemcpyAsync(g2.data(), net->gw2, sizeof(float) * g2.size(), cudaMemcpyDeviceToHost, net->stream));
+        NK(cudaMemcpyAsync(g3.data(), net->gw3, sizeof(float) * g3.size(), cudaMemcpyDeviceToHost, net->stream));
+        NK(cudaMemcpyAsync(gb.data(), net->gb, sizeof(float) * gb.size(), cudaMemcpyDeviceToHost, net->stream));
+        NK(cudaStreamSynchronize(net->stream));
+        auto unpack = [&](const std::vector<float> &src, int cout, int cin, int cinp, float *dst) {
+            for (int o = 0; o < cout; ++o)
+                for (int c = 0; c < cin; ++c)
+                    for (int t = 0; t < 27; ++t) dst[((long)o * cin + c) * 27 + t] = src[((long)o * 27 + t) * cinp + c];
+        };
+        unpack(g1, 32, 9, 16, grad_host + OFF_W1);
+        unpack(g2, 32, 32, 32, grad_host + OFF_W2);
+        unpack(g3, 6, 32, 32, grad_host + OFF_W3);
+        std::memcpy(grad_host + OFF_B1, gb.data(), sizeof(float) * 32);
+        std::memcpy(grad_host + OFF_B2, gb.data() + 32, sizeof(float) * 32);
+        std::memcpy(grad_host + OFF_B3, gb.data() + 64, sizeof(float) * 6);
+    }
+    NK(cudaStreamSynchronize(net->stream));
+    if (loss) *loss = net->hostd[0];
+    return DNS_OK;
+}
+
+int dns_net_train_step(dns_net net, int nsamples, const float *g, const float *tau, double lr, double *loss) {
+    if (!net || !g || !tau || nsamples < 1 || !(lr > 0.0)) return DNS_ERR_ARG;
+    const long long V = (long long)net->n * net->n * net->n;
+    NK(cudaMemsetAsync(net->gw1, 0, sizeof(float) * 32 * 27 * 16, net->stream));
+    NK(cudaMemsetAsync(net->gw2, 0, sizeof(float) * 32 * 27 * 32, net->stream));
+    NK(cudaMemsetAsync(net->gw3, 0, sizeof(float) * OUTP * 27 * 32, net->stream));
+    NK(cudaMemsetAsync(net->gb, 0, sizeof(float) * 72, net->stream));
+    NK(cudaMemsetAsync(net->lsum, 0, sizeof(double), net->stream));
+    for (int i = 0; i < nsamples; ++i) {
+        NK(net_forward(net, g + (long long)i * 9 * V, net->stream));
+        NK(net_backward(net, tau + (long long)i * 6 * V));
+    }
+    // Adam on the minibatch-mean gradient
+    net->step += 1;
+    const float b1 = 0.9f, b2 = 0.999f, eps = 1e-8f;
+    const float c1 = 1.f - std::pow(b1, (float)net->step), c2 = 1.f - std::pow(b2, (float)net->step);
+    const float inv = 1.f / (float)nsamples;
+    struct Blk {
+        float *g;
+        int n;
+    } grads[4] = {{net->gw1, 32 * 27 * 16}, {net->gw2, 32 * 27 * 32}, {net->gw3, OUTP * 27 * 32}, {net->gb, 72}};
+    for (auto &b : grads) k_scale<<<nblk(b.n), 256, 0, net->stream>>>(b.g, b.n, inv);
+    const float lrf = (float)lr;
+    k_adam<<<nblk(NET_W1), 256, 0, net->stream>>>(net->p + OFF_W1, net->m + OFF_W1, net->v + OFF_W1, net->gw1,
+                                                   (int)NET_W1, 1, 32, 9, 16, lrf, b1, b2, eps, c1, c2);
+    k_adam<<<1, 256, 0, net->stream>>>(net->p + OFF_B1, net->m + OFF_B1, net->v + OFF_B1, net->gb, 32, 0, 0, 0, 0,
+                                       lrf, b1, b2, eps, c1, c2);
+    k_adam<<<nblk(NET_W2), 256, 0, net->stream>>>(net->p + OFF_W2, net->m + OFF_W2, net->v + OFF_W2, net->gw2,
+                                                   (int)NET_W2, 1, 32, 32, 32, lrf, b1, b2, eps, c1, c2);
+    k_adam<<<1, 256, 0, net->stream>>>(net->p + OFF_B2, net->m + OFF_B2, net->v + OFF_B2, net->gb + 32, 32, 0, 0, 0,
+                                       0, lrf, b1, b2, eps, c1, c2);
+    k_adam<<<nblk(NET_W3), 256, 0, net->stream>>>(net->p + OFF_W3, net->m + OFF_W3, net->v + OFF_W3, net->gw3,
+                                                   (int)NET_W3, 1, 6, 32, 32, lrf, b1, b2, eps, c1, c2);
+    k_adam<<<1, 256, 0, net->stream>>>(net->p + OFF_B3, net->m + OFF_B3, net->v + OFF_B3, net->gb + 64, 6, 0, 0, 0,
+                                       0, lrf, b1, b2, eps, c1, c2);
+    NK(cudaGetLastError());
+    NK(net_pack(net));
+    if (loss) NK(cudaMemcpyAsync(net->hostd, net->lsum, sizeof(double), cudaMemcpyDeviceToHost, net->stream));
+    NK(cudaStreamSynchronize(net->stream));
+    if (loss) *loss = net->hostd[0] / nsamples;
+    (void)V;
+    return DNS_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- closure and training data
+static float2 *make_twiddles_f(int N) {
+    std::vector<float2> h(N);
+    for (int m = 0; m < N; ++m) {
+        const double a = 2.0 * M_PI * m / N;
+        h[m] = make_float2((float)std::cos(a), (float)-std::sin(a));
+    }
+    float2 *d = nullptr;
+    if (cudaMalloc(&d, sizeof(float2) * N) != cudaSuccess) return nullptr;
+    if (cudaMemcpy(d, h.data(), sizeof(float2) * N, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(d);
+        return nullptr;
+    }
+    return d;
+}
+
+namespace dns {
+struct LesClosure {
+    dns_net_ctx *net = nullptr;  // not owned
+    int n = 0;
+    float2 *tw = nullptr, *gc = nullptr, *thc = nullptr;
+    float *gr = nullptr, *tau = nullptr;
+};
+
+void les_closure_release(LesClosure *c) {
+    if (!c) return;
+    void *b[] = {c->tw, c->gc, c->thc, c->gr, c->tau};
+    for (void *p : b)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+cudaError_t les_closure_forcing(LesClosure *c, const Geo &g, const void *U, void *Fext, cudaStream_t st) {
+    const int n = c->n;
+    const long long V = (long long)n * n * n;
+    cudaError_t e;
+    k_compact_to_full_c<<<nblk(9 * V), 256, 0, st>>>(g, (const float2 *)U, c->gc, 1, 1.0f / (float)V);
+    if ((e = c2c(n, c->gc, c->tw, 9, +1, st)) != cudaSuccess) return e;
+    k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, c->net->in_scale);
+    if ((e = net_forward(c->net, c->gr, st)) != cudaSuccess) return e;
+    k_out_to_tau<<<nblk(6 * V), 256, 0, st>>>(c->net->Y3, V, c->tau, c->net->out_scale);
+    k_real_to_c<<<nblk(6 * V), 256, 0, st>>>(c->tau, 6 * V, c->thc);
+    if ((e = c2c(n, c->thc, c->tw, 6, -1, st)) != cudaSuccess) return e;
+    k_closure_forcing<<<nblk(g.sS), 256, 0, st>>>(g, c->thc, (float2 *)Fext);
+    return cudaGetLastError();
+}
+}  // namespace dns
+
+// compact N-mesh state -> full half-spectrum layout on the n mesh, |k_i| <= kc, times scale
+__global__ void k_filter_to_half(dns::Geo g, const float2 *__restrict__ U, int n, int kc, float scale,
+                                 float2 *__restrict__ out) {
+    const int nh = n / 2 + 1;
+    const long long total = 3LL * n * n * nh;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int kz = (int)(e % nh);
+    const long long r = e / nh;
+    const int iy = (int)(r % n), ix = (int)((r / n) % n), c = (int)(r / ((long long)n * n));
+    const int kx = fft_k(ix, n), ky = fft_k(iy, n);
+    float2 v = make_float2(0.f, 0.f);
+    if (abs(kx) <= kc && abs(ky) <= kc && kz <= kc && abs(kx) <= g.K && abs(ky) <= g.K && kz <= g.K) {
+        const int cx = kx >= 0 ? kx : kx + g.Kx, cy = ky >= 0 ? ky : ky + g.Kx;
+        const float2 u = U[c * g.sS + ((long long)cx * g.Kx + cy) * g.Kzp + kz];
+        v = make_float2(u.x * scale, u.y * scale);
+    }
+    out[e] = v;
+}
+
+struct dns_les_builder_ctx {
+    int N = 0, n = 0;
+    float2 *twN = nullptr, *twn = nullptr, *bigc = nullptr, *smallc = nullptr, *ubc = nullptr;
+};
+
+static void builder_release(dns_les_builder_ctx *b) {
+    if (!b) return;
+    void *p[] = {b->twN, b->twn, b->bigc, b->smallc, b->ubc};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    delete b;
+}
+
+extern "C" {
+
+int dns_les_builder_create(int N, int n, dns_les_builder *out) {
+    if (!out) return DNS_ERR_ARG;
+    *out = nullptr;
+    if (!c2c_supported(N) || !c2c_supported(n) || n > N) return DNS_ERR_UNSUPPORTED;
+    dns_les_builder_ctx *b = new (std::nothrow) dns_les_builder_ctx();
+    if (!b) return DNS_ERR_OOM;
+    b->N = N;
+    b->n = n;
+    const long long VN = (long long)N * N * N, Vn = (long long)n * n * n;
+    b->twN = make_twiddles_f(N);
+    b->twn = make_twiddles_f(n);
+    bool ok = b->twN && b->twn;
+    if (ok && cudaMalloc(&b->bigc, sizeof(float2) * 9 * VN) != cudaSuccess) { b->bigc = nullptr; ok = false; }
+    if (ok && cudaMalloc(&b->smallc, sizeof(float2) * 9 * Vn) != cudaSuccess) { b->smallc = nullptr; ok = false; }
+    if (ok && cudaMalloc(&b->ubc, sizeof(float2) * 3 * Vn) != cudaSuccess) { b->ubc = nullptr; ok = false; }
+    if (!ok) {
+        builder_release(b);
+        return DNS_ERR_OOM;
+    }
+    *out = b;
+    return DNS_OK;
+}
+
+int dns_les_builder_free(dns_les_builder b) {
+    if (b) {
+        cudaDeviceSynchronize();
+        builder_release(b);
+    }
+    return DNS_OK;
+}
+
+int dns_les_builder_run(dns_les_builder b, dns_handle dns, float *g, float *tau, void *ubar_hat) {
+    if (!b || !dns || !g || !tau) return DNS_ERR_ARG;
+    dns::InternalView v;
+    if (dns::internal_view(dns, &v) || v.N != b->N) return DNS_ERR_ARG;
+    if (v.dtype != DNS_F32) return DNS_ERR_UNSUPPORTED;
+    const int N = b->N, n = b->n, kc = (n - 1) / 3;
+    const long long VN = (long long)N * N * N, Vn = (long long)n * n * n;
+    cudaStream_t st = v.stream;
+    const float2 *U = (const float2 *)v.U0;
+    const float invN3 = 1.0f / (float)VN;
+    // u on the DNS mesh, its six products, forward
+    k_compact_to_full_c<<<nblk(3 * VN), 256, 0, st>>>(v.g, U, b->bigc, 0, invN3);
+    NK(c2c(N, b->bigc, b->twN, 3, +1, st));
+    k_products<<<nblk(6 * VN), 256, 0, st>>>(b->bigc, VN, b->bigc + 3 * VN);
+    NK(c2c(N, b->bigc + 3 * VN, b->twN, 6, -1, st));
+    // filt(u_i u_j) at the LES points: cutoff, move to the n mesh, inverse (1/N^3 folded in)
+    k_filter_full<<<nblk(6 * Vn), 256, 0, st>>>(b->bigc + 3 * VN, N, b->smallc, n, 6, kc, invN3);
+    NK(c2c(n, b->smallc, b->twn, 6, +1, st));
+    // ubar at the LES points
+    k_compact_to_full_c<<<nblk(3 * VN), 256, 0, st>>>(v.g, U, b->bigc, 0, 1.0f);
+    k_filter_full<<<nblk(3 * Vn), 256, 0, st>>>(b->bigc, N, b->ubc, n, 3, kc, invN3);
+    NK(c2c(n, b->ubc, b->twn, 3, +1, st));
+    k_tau_from_parts<<<nblk(6 * Vn), 256, 0, st>>>(b->smallc, b->ubc, Vn, tau);
+    // gradients d_j ubar_i
+    k_compact_to_full_c<<<nblk(9 * VN), 256, 0, st>>>(v.g, U, b->bigc, 1, 1.0f);
+    k_filter_full<<<nblk(9 * Vn), 256, 0, st>>>(b->bigc, N, b->smallc, n, 9, kc, invN3);
+    NK(c2c(n, b->smallc, b->twn, 9, +1, st));
+    k_real_part<<<nblk(9 * Vn), 256, 0, st>>>(b->smallc, 9 * Vn, g, 1.0f);
+    if (ubar_hat) {
+        const float scale = (float)((double)Vn / (double)VN);
+        k_filter_to_half<<<nblk(3LL * n * n * (n / 2 + 1)), 256, 0, st>>>(v.g, U, n, kc, scale, (float2 *)ubar_hat);
+    }
+    NK(cudaGetLastError());
+    NK(cudaStreamSynchronize(st));
+    return DNS_OK;
+}
+
+int dns_les_set_closure(dns_handle h, dns_net net) {
+    if (!h) return DNS_ERR_ARG;
+    if (!net) return dns::internal_set_closure(h, nullptr);
+    dns::InternalView v;
+    if (dns::internal_view(h, &v)) return DNS_ERR_ARG;
+    if (v.dtype != DNS_F32 || v.N != net->n || !c2c_supported(v.N) || v.g.nb != 1) return DNS_ERR_UNSUPPORTED;
+    dns::LesClosure *c = new (std::nothrow) dns::LesClosure();
+    if (!c) return DNS_ERR_OOM;
+    c->net = net;
+    c->n = v.N;
+    const long long V = (long long)v.N * v.N * v.N;
+    c->tw = make_twiddles_f(v.N);
+    bool ok = c->tw != nullptr;
+    if (ok && cudaMalloc(&c->gc, sizeof(float2) * 9 * V) != cudaSuccess) { c->gc = nullptr; ok = false; }
+    if (ok && cudaMalloc(&c->thc, sizeof(float2) * 6 * V) != cudaSuccess) { c->thc = nullptr; ok = false; }
+    if (ok && cudaMalloc(&c->gr, sizeof(float) * 9 * V) != cudaSuccess) { c->gr = nullptr; ok = false; }
+    if (ok && cudaMalloc(&c->tau, sizeof(float) * 6 * V) != cudaSuccess) { c->tau = nullptr; ok = false; }
+    if (!ok) {
+        dns::les_closure_release(c);
+        return DNS_ERR_OOM;
+    }
+    return dns::internal_set_closure(h, c);
+}
+
+}  // extern "C"

@@ -53,6 +53,7 @@ struct UpdateArgs {
     cacc *U0out;     // after the last stage: the new step-start state
     cacc *dU;        // stage = -1: right-hand side out
     cplx *Om;        // curl of the next stage input (stages 0..3), nullptr to skip
+    const cplx *Fext;  // extra forcing on the stored modes added before the projection, or nullptr
     double nu;
     const double *nu_box;  // per-box viscosity (batched boxes), or nullptr for nu
     double adt;      // a_s * dt
@@ -183,8 +184,8 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
 // kz); the cross product is computed inside the first forward stage, so the
 // physical values are read once from shared memory and never stored.
 template <typename real, int N, int L, int T, int MAXR>
-__global__ void __launch_bounds__(T) k_p3_z_cross(Geo g, const typename CT<real>::t *__restrict__ twg,
-                                                  typename CT<real>::t *__restrict__ B) {
+__device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                        typename CT<real>::t *__restrict__ B) {
     typedef typename CT<real>::t cplx;
     constexpr int LDR = row_ld(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -269,6 +270,19 @@ __global__ void __launch_bounds__(T) k_p3_z_cross(Geo g, const typename CT<real>
         B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
         B[2 * sB + off] = zb;
     }
+}
+
+// Two launch-bound flavours of P3 (the autotuner picks): the compiler's own
+// register choice, or a limit that keeps two blocks resident per SM.
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p3_z_cross(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                  typename CT<real>::t *__restrict__ B) {
+    p3_body<real, N, L, T, MAXR>(g, twg, B);
+}
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T, 2) k_p3_z_cross_2b(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                        typename CT<real>::t *__restrict__ B) {
+    p3_body<real, N, L, T, MAXR>(g, twg, B);
 }
 
 // ------------------------------------------------------------------- physical input
@@ -472,7 +486,13 @@ __global__ void k_p5b_update(Geo g, const typename CT<real>::t *__restrict__ Nh,
         const long long nm = box * g.bB + mm;  // N^ lives in B, state layout
         const long long m = box * g.bS + mm;   // state element, component 0
         const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
-        const cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
+        cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
+        if (args.Fext && args.stage != -2) {
+            const cplx f0 = args.Fext[m], f1 = args.Fext[sS + m], f2 = args.Fext[2 * sS + m];
+            n0 = cadd(n0, f0);
+            n1 = cadd(n1, f1);
+            n2 = cadd(n2, f2);
+        }
         if (args.stage == -2) {  // bare forward transform (physical input)
             args.dU[m] = cmk<cacc>(n0.x, n0.y);
             args.dU[sS + m] = cmk<cacc>(n1.x, n1.y);

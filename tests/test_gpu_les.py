@@ -1,0 +1,191 @@
+"""Learned LES closure on the GPU against the FP64 oracle (oracle_les.c).
+
+Tolerances: the training-data builder and the closure term are FP32
+transforms (1e-5 relative); the network runs BF16 operands with FP32
+accumulation and BF16 activations, so its outputs are compared with the
+oracle run on the same BF16-rounded weights and inputs within 2e-2 (outputs)
+and 6e-2 (gradients) relative L2 per parameter block.
+"""
+import numpy as np
+import pytest
+
+from paper_1607_00850_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def dns():
+    assert torch.cuda.is_available(), "GPU tests need cuda:0"
+    from paper_1607_00850_gb300 import build, dns as d
+    build.build()
+    d.load()
+    return d
+
+
+def rel(a, b):
+    a, b = np.asarray(a), np.asarray(b)
+    dt = np.complex128 if (np.iscomplexobj(a) or np.iscomplexobj(b)) else np.float64
+    a, b = a.astype(dt), b.astype(dt)
+    return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+def bf16(x):
+    a = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    a = (a + 0x7FFF + ((a >> 16) & 1)) & 0xFFFF0000
+    return a.astype(np.uint32).view(np.float32)
+
+
+def split(p):
+    sizes = [32 * 9 * 27, 32, 32 * 32 * 27, 32, 6 * 32 * 27, 6]
+    shapes = [(32, 9, 27), (32,), (32, 32, 27), (32,), (6, 32, 27), (6,)]
+    out, o = [], 0
+    for s, sh in zip(sizes, shapes):
+        out.append(np.asarray(p[o:o + s], np.float64).reshape(sh))
+        o += s
+    return out
+
+
+def dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+@pytest.mark.parametrize("N,n", [(32, 16), (64, 16), (32, 32)])
+def test_builder_matches_oracle(dns, orc, N, n):
+    uh = inputs.random_isotropic(N, seed=71, k0=3.0).astype(np.complex64)
+    with dns.Solver(N, 0.01, 0.01, dns.DNS_F32) as s:
+        s.set_velocity(uh)
+        b = dns.dns_les_builder_create(N, n)
+        g = torch.empty((9, n, n, n), device="cuda")
+        tau = torch.empty((6, n, n, n), device="cuda")
+        ub = torch.empty((3, n, n, n // 2 + 1), dtype=torch.complex64, device="cuda")
+        dns.dns_les_builder_run(b, s.h, g, tau, ub)
+        dns.dns_les_builder_free(b)
+    ub_ref, g_ref, tau_ref = orc.les_inputs(uh.astype(np.complex128), n)
+    assert rel(g.cpu().numpy(), g_ref) < 1e-5
+    assert rel(tau.cpu().numpy(), tau_ref) < 1e-4
+    assert rel(ub.cpu().numpy(), ub_ref) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def sample16(dns):
+    """(g, tau) of one filtered 32^3 field on the 16^3 mesh, from the GPU builder."""
+    uh = inputs.random_isotropic(32, seed=72, k0=3.0).astype(np.complex64)
+    with dns.Solver(32, 0.01, 0.01, dns.DNS_F32) as s:
+        s.set_velocity(uh)
+        b = dns.dns_les_builder_create(32, 16)
+        g = torch.empty((9, 16, 16, 16), device="cuda")
+        tau = torch.empty((6, 16, 16, 16), device="cuda")
+        dns.dns_les_builder_run(b, s.h, g, tau)
+        dns.dns_les_builder_free(b)
+    # normalise like training does: unit rms inputs and targets
+    return g / g.std(), tau / tau.std()
+
+
+def test_net_forward_matches_oracle(dns, orc, sample16):
+    g, _ = sample16
+    net = dns.dns_net_create(16, seed=3)
+    try:
+        p = dns.dns_net_get_params(net)
+        pb = p.copy()
+        for k, (o, s) in enumerate([(0, 32 * 9 * 27), (32 * 9 * 27 + 32, 32 * 32 * 27),
+                                    (32 * 9 * 27 + 64 + 32 * 32 * 27, 6 * 32 * 27)]):
+            pb[o:o + s] = bf16(p[o:o + s])     # the GPU multiplies BF16 weights
+        dns.dns_net_set_params(net, pb)
+        tau = torch.empty((6, 16, 16, 16), device="cuda")
+        dns.dns_net_forward(net, g, tau)
+        ref, _, _ = orc.net(bf16(g.cpu().numpy()), split(pb))
+        assert rel(tau.cpu().numpy(), ref) < 2e-2
+    finally:
+        dns.dns_net_free(net)
+
+
+def test_net_gradients_match_oracle(dns, orc, sample16):
+    g, t = sample16
+    net = dns.dns_net_create(16, seed=4)
+    try:
+        p = dns.dns_net_get_params(net)
+        pb = p.copy()
+        for o, s in [(0, 32 * 9 * 27), (32 * 9 * 27 + 32, 32 * 32 * 27), (32 * 9 * 27 + 64 + 32 * 32 * 27, 6 * 32 * 27)]:
+            pb[o:o + s] = bf16(p[o:o + s])
+        dns.dns_net_set_params(net, pb)
+        loss, grad = dns.dns_net_gradients(net, g, t)
+        _, loss_ref, grads_ref = orc.net(bf16(g.cpu().numpy()), split(pb), t.cpu().numpy(), grads=True)
+        assert abs(loss - loss_ref) < 2e-2 * loss_ref
+        got = split(grad)
+        for k in range(6):
+            assert rel(got[k], grads_ref[k]) < 6e-2, k
+    finally:
+        dns.dns_net_free(net)
+
+
+def test_training_reduces_loss(dns):
+    # a few Adam steps on filtered snapshots of a decaying 32^3 run
+    n, N = 16, 32
+    gs, ts = [], []
+    with dns.Solver(N, 0.005, 0.01, dns.DNS_F32) as s:
+        s.set_velocity(inputs.random_isotropic(N, seed=73, k0=3.0))
+        b = dns.dns_les_builder_create(N, n)
+        for _ in range(8):
+            g = torch.empty((9, n, n, n), device="cuda")
+            tau = torch.empty((6, n, n, n), device="cuda")
+            dns.dns_les_builder_run(b, s.h, g, tau)
+            gs.append(g)
+            ts.append(tau)
+            s.step(5)
+        dns.dns_les_builder_free(b)
+    G = torch.stack(gs)
+    Tt = torch.stack(ts)
+    G, Tt = (G / G.std()).contiguous(), (Tt / Tt.std()).contiguous()
+    net = dns.dns_net_create(n, seed=5)
+    try:
+        losses = [dns.dns_net_train_step(net, 8, G, Tt, 2e-3) for _ in range(60)]
+    finally:
+        dns.dns_net_free(net)
+    assert np.isfinite(losses).all()
+    assert losses[-1] < 0.7 * losses[0]
+
+
+def test_closure_term_matches_oracle(dns, orc, sample16):
+    # RHS with the closure attached minus RHS without = P(m(-i k_j tau_ij^)),
+    # tau = the network applied to the gradients of the same field
+    n, nu = 16, 0.01
+    ub = inputs.random_isotropic(n, seed=74, k0=3.0).astype(np.complex64)
+    net = dns.dns_net_create(n, seed=6)
+    try:
+        with dns.Solver(n, nu, 0.01, dns.DNS_F32) as s:
+            base = s.rhs(ub)
+            dns.dns_les_set_closure(s.h, net)
+            with_closure = s.rhs(ub)
+            # the same gradients through the builder at equal meshes (identity filter)
+            s.set_velocity(ub)
+            b = dns.dns_les_builder_create(n, n)
+            g = torch.empty((9, n, n, n), device="cuda")
+            tau = torch.empty((6, n, n, n), device="cuda")
+            dns.dns_les_builder_run(b, s.h, g, tau)
+            dns.dns_les_builder_free(b)
+            dns.dns_net_forward(net, g, tau)
+            dns.dns_les_set_closure(s.h, None)
+            assert np.array_equal(s.rhs(ub), base)
+    finally:
+        dns.dns_net_free(net)
+    u64 = ub.astype(np.complex128)
+    ref = orc.rhs_les(u64, nu, tau.cpu().numpy()) - orc.rhs(u64, nu)
+    got = with_closure.astype(np.complex128) - base
+    assert rel(got, ref) < 1e-4
+
+
+def test_les_step_with_closure_runs_and_decays(dns):
+    n = 32
+    net = dns.dns_net_create(n, seed=8)
+    try:
+        with dns.Solver(n, 0.005, 0.005, dns.DNS_F32) as s:
+            s.set_velocity(inputs.random_isotropic(n, seed=75, k0=3.0))
+            dns.dns_les_set_closure(s.h, net)
+            E0 = s.energy()
+            s.step(5)
+            E1 = s.energy()
+        assert np.isfinite(E1) and 0 < E1 < 1.5 * E0
+    finally:
+        dns.dns_net_free(net)
