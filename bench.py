@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--plan", default=None,
+                   help="five comma-separated pass variants; skips the autotuner (profiling runs)")
     return p.parse_args()
 
 
@@ -56,6 +58,40 @@ def config(N, dt):
                         f"nu=1/4000, CFL-0.5 dt, 2/3 dealiasing, classical RK4",
             "N": N, "nu": 1.0 / 4000.0, "dt": dt, "seed": SEED,
             "l2": "inputs larger than L2 (working set several GB); no flush"}
+
+
+KERNEL_SOURCES = ("dns_fft.cuh", "dns_passes.cuh", "dns_launch.cuh", "dns_inst.cu")
+
+
+def kernel_source_hash():
+    """sha256 over the sources of the step kernels: DRAM traffic recorded by
+    an ncu capture is used only while these files are unchanged."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1607_00850_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(N, kernel, variant):
+    """DRAM bytes (read + write) per launch of one pass, from the ncu summary
+    profiles/dram_fp32_<N>.txt, or None when there is no summary for this
+    mesh, the kernel sources changed since it was taken, or it was taken
+    with another launch variant of this pass."""
+    path = os.path.join(ROOT, "profiles", f"dram_fp32_{N}.txt")
+    try:
+        lines = open(path).read().splitlines()
+    except OSError:
+        return None
+    src = [l.split()[1] for l in lines if l.startswith("source_sha256:")]
+    if not src or src[0] != kernel_source_hash():
+        return None
+    for l in lines:
+        f = l.split()
+        if len(f) == 4 and f[0] == "traffic" and f[1] == kernel and int(f[2]) == variant:
+            return float(f[3])
+    return None
 
 
 def measured_peaks():
@@ -144,7 +180,7 @@ def pass_bytes(N, dtype, stage):
     return [p1, p2, p3, p4, p5a, rd + wr]
 
 
-PASS_NAMES = ["p1_curl_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5a_xfwd", "p5b_update"]
+PASS_NAMES = ["p1_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5a_xfwd", "p5b_update"]
 
 
 def survey_step_bytes(N, dtype):
@@ -176,7 +212,11 @@ def run_ours(args, rank, world, local_rank):
 
     s = dns.Solver(N, nu, dt, dns.DNS_F32, stream=stream.cuda_stream)
     s.set_velocity(u32)
-    plan = dns.dns_autotune(s.h)       # launch shapes picked by timing on this GPU
+    if args.plan:
+        plan = [int(v) for v in args.plan.split(",")]
+        dns.dns_set_plan(s.h, plan)
+    else:
+        plan = dns.dns_autotune(s.h)   # launch shapes picked by timing on this GPU
     shapes = {dns.PASSES[p]: dns.dns_variant_info(s.h, p, v) for p, v in enumerate(plan)}
     E0 = s.energy()
     s.step(args.warmup)
@@ -216,7 +256,8 @@ def run_ours(args, rank, world, local_rank):
     achieved = avg_bytes[dom] / (dur / 1e3) / 1e9
     step_bytes = sum(sum(p) for p in per_stage)
     roofline = {"bound": "hbm", "kernel": names[dom], "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src, "traffic": None,
+                "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": recorded_traffic(N, names[dom], plan[min(dom, 4)] if dom < 5 else 0),
                 "algorithmic_bytes_per_launch": avg_bytes[dom], "avg_launch_ms": dur,
                 "step_bytes_pruned": step_bytes,
                 "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
