@@ -74,6 +74,7 @@ class Oracle:
             "or_net": [ctypes.c_int] + [_dp] * 16,
             "or_les_inputs": [ctypes.c_int, _dp, ctypes.c_int, _dp, _dp, _dp],
             "or_rhs_les": [ctypes.c_int, ctypes.c_double, _dp, _dp, _dp],
+            "or_smagorinsky": [ctypes.c_long, _dp, ctypes.c_double, _dp],
         }.items():
             f = getattr(lib, name)
             f.argtypes = args
@@ -251,6 +252,14 @@ class Oracle:
         self._check(self.lib.or_rhs_les(ubar.shape[1], float(nu), self._ptr(ubar.view(np.float64)),
                                         self._ptr(tau), self._ptr(out.view(np.float64))), "or_rhs_les")
         return out
+
+    def smagorinsky(self, g, cs: float, delta: float) -> np.ndarray:
+        """tau[6] = -2 (cs delta)^2 |S| S_ij from gradients g[9][...] (oracle_les.c)."""
+        g = np.ascontiguousarray(g, np.float64)
+        tau = np.empty((6,) + g.shape[1:])
+        self._check(self.lib.or_smagorinsky(g[0].size, self._ptr(g), float(cs * delta) ** 2, self._ptr(tau)),
+                    "or_smagorinsky")
+        return tau
 
     def spectrum(self, uhat, nshells: int | None = None) -> np.ndarray:
         uhat = self._spec(uhat)

@@ -78,6 +78,8 @@ int or_net(int n, const double *g, const double *target, const double *w1, const
 int or_les_inputs(int N, const double *uhat, int n, double *ubar_hat, double *g, double *tau);
 /* LES right-hand side: Eq. NSfinal on ubar plus P(m (-i k_j tau_ij^)). */
 int or_rhs_les(int n, double nu, const double *ubar_hat, const double *tau, double *duhat);
+/* Smagorinsky stresses tau_ij = -2 (C_s Delta)^2 |S| S_ij from gradients g[9][np]. */
+int or_smagorinsky(long np, const double *g, double cs_delta2, double *tau);
 
 #ifdef __cplusplus
 }

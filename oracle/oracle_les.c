@@ -264,3 +264,22 @@ int or_rhs_les(int n, double nu, const double *ubar_hat, const double *tau, doub
     free(th);
     return rc;
 }
+
+/* Smagorinsky eddy-viscosity closure (the classic non-learned comparator;
+ * not in the paper): with S_ij = (d_j u_i + d_i u_j)/2 and
+ * |S| = sqrt(2 S_ij S_ij), tau_ij = -2 (C_s Delta)^2 |S| S_ij, computed
+ * pointwise from the gradients g[3i+j] = d_j u_i of the LES field. */
+int or_smagorinsky(long np, const double *g, double cs_delta2, double *tau) {
+    if (np < 1 || !g || !tau) return -1;
+    const int pi[6] = {0, 1, 2, 0, 0, 1}, pj[6] = {0, 1, 2, 1, 2, 2};
+    for (long p = 0; p < np; ++p) {
+        double S[3][3], ss = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) S[i][j] = 0.5 * (g[(3 * i + j) * np + p] + g[(3 * j + i) * np + p]);
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) ss += S[i][j] * S[i][j];
+        const double mag = sqrt(2.0 * ss);
+        for (int q = 0; q < 6; ++q) tau[q * np + p] = -2.0 * cs_delta2 * mag * S[pi[q]][pj[q]];
+    }
+    return 0;
+}

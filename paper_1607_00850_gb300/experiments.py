@@ -10,6 +10,12 @@ solution drifts from the FP64 one: the rms velocity difference
 both, every ``every`` steps.
 
     python -m paper_1607_00850_gb300.experiments tg-long --N 128 --t-end 20
+
+``les``: a learned subgrid closure trained on filtered DNS and compared a
+posteriori with no model and with Smagorinsky (not in the paper; see
+``les_closure``).
+
+    python -m paper_1607_00850_gb300.experiments les --N 256 --n 64
 """
 from __future__ import annotations
 
@@ -70,6 +76,179 @@ def tg_long(N: int = 128, t_end: float = 20.0, dt: float = 1e-3, re: float = 160
     return rows
 
 
+def _log_spectrum_error(e: np.ndarray, ref: np.ndarray, kc: int) -> float:
+    """rms of log10(E(k)/E_ref(k)) over shells 1..kc."""
+    k = np.arange(1, kc + 1)
+    return float(np.sqrt(np.mean(np.log10(np.maximum(e[k], 1e-300) / ref[k]) ** 2)))
+
+
+def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, k0: float = 4.0,
+                seeds: int = 40, snaps: int = 50, spinup: int = 100, stride: int = 1, epochs: int = 8,
+                batch: int = 8, lr: float = 1e-3, eval_steps: int = 500, eval_every: int = 50, cs: float = 0.17,
+                seed0: int = 5000, out=sys.stdout) -> dict:
+    """Learned subgrid closure for an n^3 LES fed by sharp-cutoff filtered N^3
+    DNS of decaying isotropic turbulence (not in the paper).
+
+    1. Training data: `seeds` random-phase fields (E(k) ~ k^4 exp(-2(k/k0)^2),
+       unit energy), each spun up for `spinup` DNS steps, then `snaps`
+       snapshots `stride` steps apart; each snapshot gives the 9 filtered
+       velocity gradients and 6 subgrid stresses on the LES mesh.  All of it
+       stays in device memory.
+    2. Training: the inputs and targets are scaled to unit rms (the scales
+       go into the closure); Adam on shuffled mini-batches for `epochs`
+       passes; the loss on a held-out seed is reported per epoch.
+    3. A posteriori: from the filtered field of a held-out seed, `eval_steps`
+       LES steps without a model, with Smagorinsky (C_s = cs, Delta = mesh
+       spacing) and with the learned closure, against the filtered DNS;
+       resolved energy and the log-spectrum error over k <= kc every
+       `eval_every` steps."""
+    import torch
+    kc = (n - 1) // 3
+    V = n ** 3
+    dev = torch.device("cuda")
+    t_start = time.perf_counter()
+    nsamp = seeds * snaps
+    G = torch.empty((nsamp, 9, n, n, n), device=dev)
+    T = torch.empty((nsamp, 6, n, n, n), device=dev)
+
+    def snapshots(seed, count, g_out, t_out, spin=spinup):
+        with dns.Solver(N, nu, dt, dns.DNS_F32) as s:
+            s.set_velocity(inputs.random_isotropic(N, seed=seed, k0=k0))
+            s.step(spin)
+            b = dns.dns_les_builder_create(N, n)
+            try:
+                for i in range(count):
+                    dns.dns_les_builder_run(b, s.h, g_out[i], t_out[i])
+                    s.step(stride)
+            finally:
+                dns.dns_les_builder_free(b)
+
+    for sd in range(seeds):
+        snapshots(seed0 + sd, snaps, G[sd * snaps:(sd + 1) * snaps], T[sd * snaps:(sd + 1) * snaps])
+    t_data = time.perf_counter() - t_start
+    nval = min(snaps, 16)
+    Gv = torch.empty((nval, 9, n, n, n), device=dev)
+    Tv = torch.empty((nval, 6, n, n, n), device=dev)
+    snapshots(seed0 + seeds, nval, Gv, Tv)
+    in_scale = float(1.0 / G.std().item())
+    out_scale = float(T.std().item())
+    G.mul_(in_scale)
+    T.mul_(1.0 / out_scale)
+    Gv.mul_(in_scale)
+    Tv.mul_(1.0 / out_scale)
+    torch.cuda.synchronize()
+
+    net = dns.dns_net_create(n, seed=seed0)
+    report = {"experiment": "les-closure", "N": N, "n": n, "kc": kc, "nu": nu, "dt": dt, "k0": k0,
+              "train_samples": nsamp, "spinup": spinup, "stride": stride, "batch": batch, "lr": lr,
+              "in_scale": in_scale, "out_scale": out_scale, "data_s": t_data, "epochs": []}
+    try:
+        rng = np.random.default_rng(seed0)
+        t0 = time.perf_counter()
+        nb = nsamp // batch
+        for ep in range(epochs):
+            order = torch.from_numpy(rng.permutation(nsamp)).to(dev)
+            rate = lr if ep < epochs - max(1, epochs // 4) else lr / 4
+            losses = []
+            for i in range(nb):
+                ix = order[i * batch:(i + 1) * batch]
+                losses.append(dns.dns_net_train_step(net, batch, G.index_select(0, ix), T.index_select(0, ix), rate))
+            val = float(np.mean([dns.dns_net_gradients(net, Gv[i], Tv[i], want_grad=False)[0] for i in range(nval)]))
+            row = {"epoch": ep + 1, "train_loss": float(np.mean(losses)), "val_loss": val,
+                   "wall_s": time.perf_counter() - t0}
+            report["epochs"].append(row)
+            if out is not None:
+                print(json.dumps(row), file=out, flush=True)
+        train_s = time.perf_counter() - t0
+        report["train_s"] = train_s
+        report["train_samples_per_s"] = epochs * nb * batch / train_s
+        # a-priori: correlation of predicted and true stresses on the held-out seed
+        pred = torch.empty((6, n, n, n), device=dev)
+        cors = np.zeros(6)
+        for i in range(nval):
+            dns.dns_net_forward(net, Gv[i], pred)
+            for q in range(6):
+                a, b = pred[q].flatten().double(), Tv[i, q].flatten().double()
+                a, b = a - a.mean(), b - b.mean()
+                cors[q] += float((a * b).sum() / torch.sqrt((a * a).sum() * (b * b).sum())) / nval
+        report["a_priori_correlation"] = {"xx yy zz xy xz yz".split()[q]: cors[q] for q in range(6)}
+        del G, T
+        torch.cuda.empty_cache()
+
+        # a posteriori
+        dns.dns_net_set_closure_scaling(net, in_scale, out_scale)
+        ub = torch.empty((3, n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
+        g1 = torch.empty((9, n, n, n), device=dev)
+        t1 = torch.empty((6, n, n, n), device=dev)
+        models = ("no_model", "smagorinsky", "learned")
+        hist = {m: [] for m in models + ("filtered_dns",)}
+        with dns.Solver(N, nu, dt, dns.DNS_F32) as d, dns.Solver(n, nu, dt, dns.DNS_F32) as ref, \
+                dns.Solver(n, nu, dt, dns.DNS_F32) as a, dns.Solver(n, nu, dt, dns.DNS_F32) as sm, \
+                dns.Solver(n, nu, dt, dns.DNS_F32) as le:
+            b = dns.dns_les_builder_create(N, n)
+            try:
+                d.set_velocity(inputs.random_isotropic(N, seed=seed0 + seeds + 1, k0=k0))
+                d.step(spinup)
+                dns.dns_les_builder_run(b, d.h, g1, t1, ub)
+                for s in (a, sm, le):
+                    s.set_velocity(ub)
+                dns.dns_les_set_smagorinsky(sm.h, cs)
+                dns.dns_les_set_closure(le.h, net)
+                done = 0
+                while True:
+                    dns.dns_les_builder_run(b, d.h, g1, t1, ub)
+                    ref.set_velocity(ub)
+                    eref = ref.spectrum()
+                    hist["filtered_dns"].append({"step": done, "E": ref.energy()})
+                    for m, s in zip(models, (a, sm, le)):
+                        e = s.spectrum()
+                        hist[m].append({"step": done, "E": s.energy(),
+                                        "log_spectrum_err": _log_spectrum_error(e, eref, kc)})
+                    if done >= eval_steps:
+                        final = {m: s.spectrum()[:kc + 2].tolist() for m, s in zip(models, (a, sm, le))}
+                        final["filtered_dns"] = eref[:kc + 2].tolist()
+                        break
+                    k = min(eval_every, eval_steps - done)
+                    for s in (d, a, sm, le):
+                        s.step(k)
+                    done += k
+                dns.dns_les_set_closure(le.h, None)
+            finally:
+                dns.dns_les_builder_free(b)
+        # cost of one LES step with and without the learned closure
+        with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
+            s.set_velocity(ub)
+            cost = {}
+            for name in ("no_model", "learned", "smagorinsky"):
+                if name == "learned":
+                    dns.dns_les_set_closure(s.h, net)
+                elif name == "smagorinsky":
+                    dns.dns_les_set_smagorinsky(s.h, cs)
+                s.step(3)
+                s.synchronize()
+                tt = time.perf_counter()
+                s.step(20)
+                s.synchronize()
+                cost[name + "_ms_per_step"] = (time.perf_counter() - tt) / 20 * 1e3
+                dns.dns_les_set_closure(s.h, None)
+        with dns.Solver(N, nu, dt, dns.DNS_F32) as s:
+            s.set_velocity(inputs.random_isotropic(N, seed=1, k0=k0))
+            s.step(3)
+            s.synchronize()
+            tt = time.perf_counter()
+            s.step(20)
+            s.synchronize()
+            cost["dns_ms_per_step"] = (time.perf_counter() - tt) / 20 * 1e3
+    finally:
+        dns.dns_net_free(net)
+    report["a_posteriori"] = {m: hist[m][-1] for m in hist}
+    report["history"] = hist
+    report["final_spectra"] = final
+    report["cost"] = cost
+    report["wall_s"] = time.perf_counter() - t_start
+    return report
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     sub = p.add_subparsers(dest="cmd", required=True)
@@ -79,7 +258,30 @@ def main(argv=None):
     q.add_argument("--dt", type=float, default=1e-3)
     q.add_argument("--every", type=int, default=1000)
     q.add_argument("--ifrk4", action="store_true")
+    q = sub.add_parser("les")
+    q.add_argument("--N", type=int, default=256)
+    q.add_argument("--n", type=int, default=64)
+    q.add_argument("--seeds", type=int, default=40)
+    q.add_argument("--snaps", type=int, default=50)
+    q.add_argument("--spinup", type=int, default=100)
+    q.add_argument("--stride", type=int, default=1)
+    q.add_argument("--epochs", type=int, default=8)
+    q.add_argument("--batch", type=int, default=8)
+    q.add_argument("--lr", type=float, default=1e-3)
+    q.add_argument("--eval-steps", type=int, default=500)
+    q.add_argument("--out", default=None, help="write the full report (JSON) here")
     args = p.parse_args(argv)
+    if args.cmd == "les":
+        dns.load()
+        rep = les_closure(args.N, args.n, seeds=args.seeds, snaps=args.snaps, spinup=args.spinup,
+                          stride=args.stride, epochs=args.epochs, batch=args.batch, lr=args.lr,
+                          eval_steps=args.eval_steps)
+        if args.out:
+            with open(args.out, "w") as f:
+                json.dump(rep, f)
+        print(json.dumps({k: v for k, v in rep.items() if k not in ("history", "final_spectra", "epochs")}),
+              flush=True)
+        return
     if args.cmd == "tg-long":
         rows = tg_long(args.N, args.t_end, args.dt, every=args.every,
                        integrator=dns.DNS_IFRK4 if args.ifrk4 else dns.DNS_RK4)

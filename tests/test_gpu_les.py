@@ -189,3 +189,35 @@ def test_les_step_with_closure_runs_and_decays(dns):
         assert np.isfinite(E1) and 0 < E1 < 1.5 * E0
     finally:
         dns.dns_net_free(net)
+
+
+def test_smagorinsky_closure_matches_oracle(dns, orc):
+    n, nu, cs = 16, 0.01, 0.17
+    ub = inputs.random_isotropic(n, seed=76, k0=3.0).astype(np.complex64)
+    with dns.Solver(n, nu, 0.01, dns.DNS_F32) as s:
+        base = s.rhs(ub)
+        dns.dns_les_set_smagorinsky(s.h, cs)
+        got = s.rhs(ub)
+        dns.dns_les_set_closure(s.h, None)
+        assert np.array_equal(s.rhs(ub), base)
+    u64 = ub.astype(np.complex128)
+    _, g, _ = orc.les_inputs(u64, n)
+    ref = orc.rhs_les(u64, nu, orc.smagorinsky(g, cs, 2 * np.pi / n)) - orc.rhs(u64, nu)
+    assert rel(got.astype(np.complex128) - base, ref) < 1e-4
+
+
+def test_smagorinsky_dissipates(dns):
+    n, nu, dt = 32, 0.002, 0.005
+    u0 = inputs.random_isotropic(n, seed=77, k0=4.0)
+    E = {}
+    for cs in (0.0, 0.17):
+        with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
+            s.set_velocity(u0)
+            if cs:
+                dns.dns_les_set_smagorinsky(s.h, cs)
+            s.step(20)
+            E[cs] = s.energy()
+    assert np.isfinite(E[0.17]) and E[0.17] < E[0.0]
+    with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
+        with pytest.raises(dns.DnsError):
+            dns.dns_les_set_smagorinsky(s.h, -0.1)

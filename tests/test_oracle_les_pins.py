@@ -137,3 +137,77 @@ def test_les_rhs_closure_term_closed_form(orc):
     tau_iso = np.zeros((6, n, n, n))
     tau_iso[0] = tau_iso[1] = tau_iso[2] = np.cos(Y) ** 2
     assert np.abs(orc.rhs_les(ub, nu, tau_iso) - base).max() < 1e-10
+
+
+# ---------------------------------------------------------------- Smagorinsky (comparator closure)
+def test_smagorinsky_plane_shear_closed_form(orc):
+    # u = (A sin z, 0, 0): S_xz = A cos z / 2, |S| = |A cos z|, so
+    # tau_xz = -(cs delta)^2 A^2 |cos z| cos z and every other component is 0
+    n, A, cs, delta = 8, 1.7, 0.17, 2 * np.pi / 8
+    zs = 2 * np.pi * np.arange(n) / n
+    Z = np.meshgrid(zs, zs, zs, indexing="ij")[2]
+    g = np.zeros((9, n, n, n))
+    g[2] = A * np.cos(Z)                       # d_z u_x
+    tau = orc.smagorinsky(g, cs, delta)
+    expect = -(cs * delta) ** 2 * A ** 2 * np.abs(np.cos(Z)) * np.cos(Z)
+    assert np.abs(tau[4] - expect).max() < 1e-15
+    assert np.abs(tau[[0, 1, 2, 3, 5]]).max() == 0
+
+
+def test_smagorinsky_invariants(orc):
+    rng = np.random.default_rng(8)
+    g = rng.standard_normal((9, 5, 5, 5))
+    g[8] = -g[0] - g[4]                        # traceless (solenoidal)
+    cs, delta = 0.2, 0.3
+    tau = orc.smagorinsky(g, cs, delta)
+    G = g.reshape(3, 3, -1)
+    S = 0.5 * (G + G.transpose(1, 0, 2))
+    T = np.empty_like(S)
+    for q, (i, j) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        T[i, j] = T[j, i] = tau[q].ravel()
+    mag = np.sqrt(2 * np.einsum("ijp,ijp->p", S, S))
+    assert np.abs(np.einsum("iip->p", T)).max() < 1e-14                    # traceless
+    # tau_ij S_ij = -(cs delta)^2 |S|^3 (pointwise dissipation)
+    assert np.allclose(np.einsum("ijp,ijp->p", T, S), -(cs * delta) ** 2 * mag ** 3, rtol=1e-13, atol=0)
+    # a pure rotation (antisymmetric gradient) has no stress
+    W = 0.5 * (G - G.transpose(1, 0, 2))
+    assert np.abs(orc.smagorinsky(W.reshape(9, 5, 5, 5), cs, delta)).max() == 0
+    # frame invariance: tau(R g R^T) = R tau(g) R^T
+    Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+    Gr = np.einsum("ai,ijp,bj->abp", Q, G, Q)
+    tr = orc.smagorinsky(Gr.reshape(9, 5, 5, 5), cs, delta)
+    Tr = np.einsum("ai,ijp,bj->abp", Q, T, Q)
+    for q, (i, j) in enumerate([(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]):
+        assert np.allclose(tr[q].ravel(), Tr[i, j], atol=1e-13)
+
+
+def test_closure_energy_rate_identity(orc):
+    # for a masked solenoidal field and any symmetric stress, the closure term
+    # changes the energy at the rate <g_ij tau_ij> (spectral derivative by parts);
+    # with Smagorinsky stresses that rate is -(cs delta)^2 <|S|^3>
+    n, nu = 12, 0.01
+    ub = inputs.random_box(n, seed=9)
+    k = np.fft.fftfreq(n, 1.0 / n)
+    kz = np.arange(n // 2 + 1)
+    KX, KY, KZ = np.meshgrid(k, k, kz, indexing="ij")
+    g = np.stack([np.fft.irfftn(1j * kj * ub[i], s=(n, n, n)) for i in range(3) for kj in (KX, KY, KZ)])
+    w = np.where((KZ == 0) | (KZ == n // 2), 1.0, 2.0)
+
+    def rate(du):
+        return float(np.sum(w * np.real(np.conj(ub) * du)) / n ** 6)
+
+    base = orc.rhs(ub, nu)
+    rng = np.random.default_rng(10)
+    tau = rng.standard_normal((6, n, n, n))
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    mean_gt = sum(np.mean((g[3 * i + j] + (g[3 * j + i] if i != j else 0)) * tau[q]) for q, (i, j) in enumerate(pairs))
+    got = rate(orc.rhs_les(ub, nu, tau) - base)
+    assert abs(got - mean_gt) < 1e-12 * abs(mean_gt) + 1e-15
+    cs, delta = 0.17, 2 * np.pi / n
+    ts = orc.smagorinsky(g, cs, delta)
+    G = g.reshape(3, 3, -1)
+    S = 0.5 * (G + G.transpose(1, 0, 2))
+    mag = np.sqrt(2 * np.einsum("ijp,ijp->p", S, S))
+    expect = -(cs * delta) ** 2 * np.mean(mag ** 3)
+    got = rate(orc.rhs_les(ub, nu, ts) - base)
+    assert expect < 0 and abs(got - expect) < 1e-11 * abs(expect)
