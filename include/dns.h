@@ -116,7 +116,10 @@ int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms);
 enum dns_integrator { DNS_RK4 = 0, DNS_IFRK4 = 1 };
 int dns_set_integrator(dns_handle h, int kind);
 
-/* Wait for the handle's queued work; reports device errors. */
+/* Wait for the handle's queued work; reports device errors, and
+ * DNS_ERR_TIMEOUT when a kernel gave up one of its bounded waits (a bulk
+ * copy into shared memory that did not complete within one second; the
+ * state is then not trustworthy and the status stays set). */
 int dns_synchronize(dns_handle h);
 
 /* Diagnostics of the current state, accumulated in double (synchronising):
@@ -179,6 +182,7 @@ int dns_ensemble_set_velocity(dns_ensemble e, int box, const void *uhat, int on_
 int dns_ensemble_get_velocity(dns_ensemble e, int box, void *uhat, int on_device);
 /* Advance every box n RK4 steps (asynchronous graph replays). */
 int dns_ensemble_step(dns_ensemble e, int n);
+/* As dns_synchronize, for every box. */
 int dns_ensemble_synchronize(dns_ensemble e);
 /* Kinetic energy of every box, E[0..nbox-1] (double accumulation).  Returns
  * DNS_ERR_NONFINITE if any is not finite. */
@@ -241,6 +245,13 @@ int dns_les_builder_run(dns_les_builder b, dns_handle dns, float *g, float *tau,
  * dns_step and dns_rhs add the closure term, evaluated from each stage's
  * input.  The handle does not own the network. */
 int dns_les_set_closure(dns_handle h, dns_net net);
+/* Attach the Smagorinsky eddy-viscosity closure instead (the classic
+ * non-learned comparator; not in the paper): tau_ij = -2 (cs delta)^2 |S| S_ij
+ * from the stage input's resolved strain S_ij, |S| = sqrt(2 S_ij S_ij);
+ * delta <= 0 selects the mesh spacing 2 pi / N.  Detach with
+ * dns_les_set_closure(h, NULL).  Same handle restrictions as above;
+ * DNS_ERR_ARG for cs < 0 or non-finite arguments. */
+int dns_les_set_smagorinsky(dns_handle h, double cs, double delta);
 
 /* ------------------------------------------------------------------------
  * Diagnostics without allocation.  The paper has no counterpart: this is a

@@ -671,7 +671,8 @@ static float2 *make_twiddles_f(int N) {
 
 namespace dns {
 struct LesClosure {
-    dns_net_ctx *net = nullptr;  // not owned
+    dns_net_ctx *net = nullptr;  // not owned; null selects the Smagorinsky stresses
+    float smag_c2 = 0.f;         // (C_s Delta)^2 of the Smagorinsky model
     int n = 0;
     float2 *tw = nullptr, *gc = nullptr, *thc = nullptr;
     float *gr = nullptr, *tau = nullptr;
@@ -691,9 +692,14 @@ cudaError_t les_closure_forcing(LesClosure *c, const Geo &g, const void *U, void
     cudaError_t e;
     k_compact_to_full_c<<<nblk(9 * V), 256, 0, st>>>(g, (const float2 *)U, c->gc, 1, 1.0f / (float)V);
     if ((e = c2c(n, c->gc, c->tw, 9, +1, st)) != cudaSuccess) return e;
-    k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, c->net->in_scale);
-    if ((e = net_forward(c->net, c->gr, st)) != cudaSuccess) return e;
-    k_out_to_tau<<<nblk(6 * V), 256, 0, st>>>(c->net->Y3, V, c->tau, c->net->out_scale);
+    if (c->net) {
+        k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, c->net->in_scale);
+        if ((e = net_forward(c->net, c->gr, st)) != cudaSuccess) return e;
+        k_out_to_tau<<<nblk(6 * V), 256, 0, st>>>(c->net->Y3, V, c->tau, c->net->out_scale);
+    } else {
+        k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, 1.0f);
+        k_smagorinsky<<<nblk(V), 256, 0, st>>>(c->gr, V, c->smag_c2, c->tau);
+    }
     k_real_to_c<<<nblk(6 * V), 256, 0, st>>>(c->tau, 6 * V, c->thc);
     if ((e = c2c(n, c->thc, c->tw, 6, -1, st)) != cudaSuccess) return e;
     k_closure_forcing<<<nblk(g.sS), 256, 0, st>>>(g, c->thc, (float2 *)Fext);
@@ -804,15 +810,12 @@ int dns_les_builder_run(dns_les_builder b, dns_handle dns, float *g, float *tau,
     return DNS_OK;
 }
 
-int dns_les_set_closure(dns_handle h, dns_net net) {
-    if (!h) return DNS_ERR_ARG;
-    if (!net) return dns::internal_set_closure(h, nullptr);
-    dns::InternalView v;
-    if (dns::internal_view(h, &v)) return DNS_ERR_ARG;
-    if (v.dtype != DNS_F32 || v.N != net->n || !c2c_supported(v.N) || v.g.nb != 1) return DNS_ERR_UNSUPPORTED;
+// Buffers of a closure on the N^3 mesh of handle view v (net or Smagorinsky).
+static int closure_attach(dns_handle h, const dns::InternalView &v, dns_net net, float smag_c2) {
     dns::LesClosure *c = new (std::nothrow) dns::LesClosure();
     if (!c) return DNS_ERR_OOM;
     c->net = net;
+    c->smag_c2 = smag_c2;
     c->n = v.N;
     const long long V = (long long)v.N * v.N * v.N;
     c->tw = make_twiddles_f(v.N);
@@ -826,6 +829,24 @@ int dns_les_set_closure(dns_handle h, dns_net net) {
         return DNS_ERR_OOM;
     }
     return dns::internal_set_closure(h, c);
+}
+
+int dns_les_set_closure(dns_handle h, dns_net net) {
+    if (!h) return DNS_ERR_ARG;
+    if (!net) return dns::internal_set_closure(h, nullptr);
+    dns::InternalView v;
+    if (dns::internal_view(h, &v)) return DNS_ERR_ARG;
+    if (v.dtype != DNS_F32 || v.N != net->n || !c2c_supported(v.N) || v.g.nb != 1) return DNS_ERR_UNSUPPORTED;
+    return closure_attach(h, v, net, 0.f);
+}
+
+int dns_les_set_smagorinsky(dns_handle h, double cs, double delta) {
+    if (!h || !(cs >= 0.0) || !std::isfinite(cs) || !std::isfinite(delta)) return DNS_ERR_ARG;
+    dns::InternalView v;
+    if (dns::internal_view(h, &v)) return DNS_ERR_ARG;
+    if (v.dtype != DNS_F32 || !c2c_supported(v.N) || v.g.nb != 1) return DNS_ERR_UNSUPPORTED;
+    const double d = delta > 0.0 ? delta : 2.0 * M_PI / v.N;
+    return closure_attach(h, v, nullptr, (float)(cs * cs * d * d));
 }
 
 }  // extern "C"

@@ -137,6 +137,27 @@ __global__ void k_real_to_c(const float *__restrict__ a, long long n, float2 *__
     if (e < n) out[e] = make_float2(a[e], 0.f);
 }
 
+// Smagorinsky stresses (the classic eddy-viscosity comparator, not in the
+// paper): S_ij = (g_ij + g_ji)/2 with g[3i+j] = d_j u_i, |S| = sqrt(2 S_ij S_ij),
+// tau_q = -2 c2 |S| S_q for q = xx, yy, zz, xy, xz, yz, c2 = (C_s Delta)^2.
+__global__ void k_smagorinsky(const float *__restrict__ g, long long V, float c2, float *__restrict__ tau) {
+    const long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (p >= V) return;
+    float a[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) a[q] = g[q * V + p];
+    const float sxx = a[0], syy = a[4], szz = a[8];
+    const float sxy = 0.5f * (a[1] + a[3]), sxz = 0.5f * (a[2] + a[6]), syz = 0.5f * (a[5] + a[7]);
+    const float ss = sxx * sxx + syy * syy + szz * szz + 2.f * (sxy * sxy + sxz * sxz + syz * syz);
+    const float f = -2.f * c2 * sqrtf(2.f * ss);
+    tau[p] = f * sxx;
+    tau[V + p] = f * syy;
+    tau[2 * V + p] = f * szz;
+    tau[3 * V + p] = f * sxy;
+    tau[4 * V + p] = f * sxz;
+    tau[5 * V + p] = f * syz;
+}
+
 // Closure forcing on the stored modes of the LES mesh: f_i = -i k_j tau_ij^
 // from the forward-transformed stresses (full complex [6][n][n][n]); the
 // update pass projects it together with the nonlinear term.

@@ -70,6 +70,7 @@ SIGNATURES = {
     "dns_les_builder_free": (_i, [_vp]),
     "dns_les_builder_run": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "dns_les_set_closure": (_i, [_vp, _vp]),
+    "dns_les_set_smagorinsky": (_i, [_vp, _d, _d]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -522,6 +523,11 @@ def dns_les_builder_run(b: int, dns_h: int, g, tau, ubar_hat=None) -> None:
 
 def dns_les_set_closure(h: int, net: int | None) -> None:
     _check(load().dns_les_set_closure(h, net), "dns_les_set_closure")
+
+
+def dns_les_set_smagorinsky(h: int, cs: float, delta: float = 0.0) -> None:
+    """Smagorinsky closure tau = -2 (cs delta)^2 |S| S; delta <= 0: mesh spacing."""
+    _check(load().dns_les_set_smagorinsky(h, float(cs), float(delta)), "dns_les_set_smagorinsky")
 
 
 def dns_net_set_closure_scaling(net: int, in_scale: float, out_scale: float) -> None:
