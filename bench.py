@@ -190,6 +190,22 @@ def survey_step_bytes(N, dtype):
     return 216 * N * N * (N // 2 + 1) * cr
 
 
+def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
+    """The largest x over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, N: int, steps: int, seconds: float) -> float:
+    """Grid-point-steps per second of the whole job: every rank advances its
+    own N^3 box (replicas), all timed by the slowest rank."""
+    return world * float(N) ** 3 * steps / seconds
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     from paper_1607_00850_gb300 import build, dns
@@ -237,15 +253,12 @@ def run_ours(args, rank, world, local_rank):
     # ---- per-kernel durations: K plain-launched steps with events on the same stream
     pass_ms, prof_total = dns.dns_step_profiled(s.h, args.steps)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist)
     steps_done = args.warmup + 2 * args.steps
     E32 = s.energy()
     s.close()
 
-    value = world * float(N) ** 3 * args.steps / (ms / 1e3)
+    value = whole_job_rate(world, N, args.steps, ms / 1e3)
     peak, peak_src = measured_peaks()
     launches = 4 * args.steps
     per_stage = [pass_bytes(N, 0, st) for st in range(4)]
@@ -285,12 +298,9 @@ def run_ours(args, rank, world, local_rank):
     t1 = time.perf_counter()
     s.close()
     e2e_s = t1 - t0
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, dist)
     nbytes = int(hin.numel() * hin.element_size())
-    e2e = {"value": world * float(N) ** 3 * ke / e2e_s, "unit": "grid-point-steps/s",
+    e2e = {"value": whole_job_rate(world, N, ke, e2e_s), "unit": "grid-point-steps/s",
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes, "steps": ke}
 
     # ---- FP64 and mixed precision side by side (same workload, fewer steps)
