@@ -180,6 +180,21 @@ def pass_bytes(N, dtype, stage):
     return [p1, p2, p3, p4, p5a, rd + wr]
 
 
+def step_flops(N):
+    """Nominal transform flops of one pruned RK4 step: 5 n log2 n per complex
+    line of length n (the textbook count), over the lines each pass transforms
+    (P1: 6 Ky Kz, P2: 6 N Kz, P3: 5 N^2 packed lines, P4: 3 N Kz, P5a: 3 Ky Kz),
+    times 4 stages.  The pointwise work (curl, cross product, projection,
+    update) adds < 2 % and is left out."""
+    import math
+    K = (N - 1) // 3
+    Ky, Kz = 2 * K + 1, K + 1
+    line = 5.0 * N * math.log2(N)
+    return 4 * line * (6 * Ky * Kz + 6 * N * Kz + 5 * N * N + 3 * N * Kz + 3 * Ky * Kz)
+
+
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 peak is available)
+
 PASS_NAMES = ["p1_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5a_xfwd", "p5b_update"]
 
 
@@ -324,6 +339,12 @@ def run_ours(args, rank, world, local_rank):
             s.close()
             extra[name] = {"value": float(N) ** 3 * k64 / (m64 / 1e3), "ms_per_step": m64 / k64,
                            "steps_timed": k64, "energy_after_steps": E}
+            if name == "fp64":
+                tf = step_flops(N) / (m64 / k64 / 1e3) / 1e12
+                extra[name]["roofline"] = {"bound": "alu", "achieved": tf, "peak": FP64_NOMINAL_TFLOPS,
+                                           "unit": "TFLOP/s", "frac": tf / FP64_NOMINAL_TFLOPS,
+                                           "peak_source": "nominal FP64 rate",
+                                           "flops_per_step": step_flops(N)}
         Eref = extra["fp64"]["energy_after_steps"]
         extra["fp32_energy_rel_err_vs_fp64"] = abs(E32 - Eref) / Eref
         extra["energy_steps"] = steps_done

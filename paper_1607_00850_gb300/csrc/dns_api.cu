@@ -49,6 +49,7 @@ struct dns_ctx {
     void *Om = nullptr, *rom = nullptr;  // curl of the stage input (state boxes / rhs input)
     double *partials = nullptr, *sums = nullptr, *Ek = nullptr;
     double *nu_box = nullptr;  // per-box viscosity when several boxes share the context
+    int *err = nullptr;        // device status word of bounded waits (Geo::err)
     int nblk = 0, smax = 0;
     double *host = nullptr;  // pinned read-back area
     cudaGraph_t graph = nullptr;
@@ -81,7 +82,7 @@ static void release(dns_ctx *h) {
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
     void *bufs[] = {h->U, h->U0, h->U1, h->A, h->B, h->io, h->rin, h->rout, h->tw, h->partials, h->sums, h->Ek,
-                    h->nu_box, h->Om, h->rom};
+                    h->nu_box, h->Om, h->rom, h->err};
     for (void *p : bufs)
         if (p) cudaFree(p);
     if (h->host) cudaFreeHost(h->host);
@@ -326,6 +327,8 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
     if (!rc) rc = dev_alloc(h, (void **)&h->sums, sizeof(double) * 2);
     if (!rc) rc = dev_alloc(h, (void **)&h->Ek, sizeof(double) * h->smax);
     if (!rc && nb > 1) rc = dev_alloc(h, (void **)&h->nu_box, sizeof(double) * nb);
+    if (!rc) rc = dev_alloc(h, (void **)&h->err, sizeof(int));
+    g.err = h->err;
     if (!rc && cudaMallocHost((void **)&h->host, sizeof(double) * (4 + h->smax)) != cudaSuccess) {
         h->host = nullptr;
         rc = DNS_ERR_OOM;
@@ -361,6 +364,7 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
     }
     if (e == cudaSuccess && nb > 1)
         e = cudaMemcpy(h->nu_box, nu_host, sizeof(double) * nb, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, nb * 3 * g.sS * h->creal, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, nb * 3 * g.sS * h->cacc, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, nb * 3 * g.sS * h->cacc, h->stream);
@@ -411,10 +415,18 @@ int dns_free(dns_handle h) {
     return DNS_OK;
 }
 
+// After the stream has drained: DNS_ERR_TIMEOUT if a kernel gave up a
+// bounded wait (the word stays set; the state is then not trustworthy).
+static int poll_device_status(dns_ctx *h) {
+    int v = 0;
+    CK(cudaMemcpy(&v, h->err, sizeof(int), cudaMemcpyDeviceToHost));
+    return v ? DNS_ERR_TIMEOUT : DNS_OK;
+}
+
 int dns_synchronize(dns_handle h) {
     if (!h) return DNS_ERR_ARG;
     CK(cudaStreamSynchronize(h->stream));
-    return DNS_OK;
+    return poll_device_status(h);
 }
 
 int dns_set_velocity(dns_handle h, const void *uhat, int on_device) {
@@ -936,6 +948,10 @@ int dns_ensemble_step(dns_ensemble e, int n) {
 int dns_ensemble_synchronize(dns_ensemble e) {
     if (!e) return DNS_ERR_ARG;
     CK(cudaStreamSynchronize(e->stream));
+    for (dns_ctx *c : e->cls) {
+        const int rc = poll_device_status(c);
+        if (rc) return rc;
+    }
     return DNS_OK;
 }
 

@@ -288,7 +288,9 @@ struct TileFFT {
 __host__ __device__ constexpr int row_ld(int N) { return N + N / 16; }
 __device__ __forceinline__ int radd(int n) { return n + (n >> 4); }
 
-template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0>
+// ONE = true runs stage S alone (its output stays in the tile unless S is
+// the last stage), so a caller can act between the first stage and the rest.
+template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0, bool ONE = false>
 struct RowFFT {
     typedef typename CT<real>::t cplx;
     // Load(v, n): first-stage input; Store(v, n, x): last-stage output.
@@ -344,7 +346,7 @@ struct RowFFT {
             }
         }
         __syncthreads();
-        if constexpr (!last) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1>::run(tile, tw, load, store);
+        if constexpr (!last && !ONE) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1>::run(tile, tw, load, store);
     }
 };
 

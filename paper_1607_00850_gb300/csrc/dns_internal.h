@@ -30,7 +30,7 @@ typedef cudaError_t (*Prep)();
 // (nullptr where a shape is not compiled) and the untuned kernels.
 struct PassSet {
     static constexpr int NCOLV = 3;  // column-pass variants (W, RC)
-    static constexpr int NP3V = 6;   // z-pass variants (L, R3)
+    static constexpr int NP3V = 11;   // z-pass variants (L, R3, resident blocks, async feed)
     ColP1 p1[NCOLV] = {};
     ColPass p2[NCOLV] = {}, p4[NCOLV] = {}, p5a[NCOLV] = {};
     Prep prep_col[NCOLV] = {};

@@ -21,22 +21,27 @@ constexpr size_t kMaxSmem = 227 * 1024;
 
 template <typename real> struct VariantTable;
 // P3 variants: lines per block lmax >> p3S (lmax = the most lines that fit
-// 512 threads), radix cap p3R, blocks the compiler keeps resident p3M.
+// 512 threads), radix cap p3R, blocks the compiler keeps resident p3M, and
+// how the input arrives, p3A: 0 loads by the threads, 1 persistent blocks
+// fed by bulk asynchronous copies (next group prefetched), 2 one group per
+// block by one bulk copy into the tile.
 template <> struct VariantTable<float> {
     static constexpr int BUD = 32;
     static constexpr int colW[3] = {16, 32, 16};
     static constexpr int colR[3] = {16, 16, 8};
-    static constexpr int p3S[6] = {0, 0, 1, 1, 2, 0};
-    static constexpr int p3R[6] = {32, 32, 32, 32, 32, 16};
-    static constexpr int p3M[6] = {1, 2, 1, 2, 2, 1};
+    static constexpr int p3S[11] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1};
+    static constexpr int p3R[11] = {32, 32, 32, 32, 32, 16, 32, 32, 32, 32, 32};
+    static constexpr int p3M[11] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2};
+    static constexpr int p3A[11] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2};
 };
 template <> struct VariantTable<double> {
     static constexpr int BUD = 16;
     static constexpr int colW[3] = {8, 16, 8};
     static constexpr int colR[3] = {8, 8, 16};
-    static constexpr int p3S[6] = {0, 0, 1, 1, 2, 0};
-    static constexpr int p3R[6] = {16, 16, 16, 16, 16, 8};
-    static constexpr int p3M[6] = {1, 2, 1, 2, 2, 1};
+    static constexpr int p3S[11] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1};
+    static constexpr int p3R[11] = {16, 16, 16, 16, 16, 8, 16, 16, 16, 16, 16};
+    static constexpr int p3M[11] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2};
+    static constexpr int p3A[11] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2};
 };
 
 __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
@@ -71,7 +76,10 @@ template <typename real, int N, int V> struct P3Shape {
     static constexpr int R3 = VT::p3R[V];
     static constexpr int T = at_least_32(raw_threads(N, 3 * L, VT::BUD));
     typedef typename CT<real>::t cplx;
-    static constexpr size_t smem = sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
+    static constexpr bool ASYNC = VT::p3A[V] == 1;
+    static constexpr bool BULK = VT::p3A[V] == 2;
+    static constexpr size_t smem =
+        ASYNC ? P3Stage<real, N, L>::smem : sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
     static constexpr int MINB = VT::p3M[V];
     static constexpr bool valid = (V == 0 || (N >= 64 && (lmax >> VT::p3S[V]) >= 1)) && T <= 1024 &&
                                   smem <= kMaxSmem && (MINB == 1 || (2 * smem <= kMaxSmem && 2 * T <= 1024));
@@ -136,17 +144,57 @@ template <typename real, int N, int V> struct ColLaunch {
 template <typename real, int N, int V> struct P3Launch {
     typedef P3Shape<real, N, V> S;
     typedef typename CT<real>::t cplx;
+    typedef void (*TmaKernel)(Geo, const cplx *, cplx *, long long);
+    static inline int resident = 0;  // persistent grid: SMs x blocks per SM (set by prepare)
+    static TmaKernel tma_kernel() {
+        if constexpr (S::MINB == 2) return k_p3_z_tma_2b<real, N, S::L, S::T, S::R3>;
+        else return k_p3_z_tma<real, N, S::L, S::T, S::R3>;
+    }
     static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
-        dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
-        if constexpr (S::MINB == 2)
-            k_p3_z_cross_2b<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
-        else
-            k_p3_z_cross<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
+        if constexpr (S::ASYNC) {
+            // bulk copies need 16-byte aligned rows of the stated padding
+            if (g.Kzp != P3Stage<real, N, S::L>::KZP || ((uintptr_t)B & 15) || resident < 1)
+                return cudaErrorInvalidValue;
+            const long long groups = (long long)N * N / S::L * g.nb;
+            const unsigned grid = (unsigned)(groups < resident ? groups : resident);
+            tma_kernel()<<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B, groups);
+        } else if constexpr (S::BULK) {
+            if (g.Kzp != P3Stage<real, N, S::L>::KZP || ((uintptr_t)B & 15)) return cudaErrorInvalidValue;
+            dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
+            if constexpr (S::MINB == 2)
+                k_p3_z_bulk_2b<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+                                                                                      (cplx *)B);
+            else
+                k_p3_z_bulk<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+                                                                                   (cplx *)B);
+        } else {
+            dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
+            if constexpr (S::MINB == 2)
+                k_p3_z_cross_2b<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+                                                                                       (cplx *)B);
+            else
+                k_p3_z_cross<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+                                                                                    (cplx *)B);
+        }
         return cudaGetLastError();
     }
     static cudaError_t prepare() {
-        if constexpr (S::MINB == 2) return set_smem(k_p3_z_cross_2b<real, N, S::L, S::T, S::R3>, S::smem);
-        else return set_smem(k_p3_z_cross<real, N, S::L, S::T, S::R3>, S::smem);
+        if constexpr (S::ASYNC) {
+            cudaError_t e = set_smem(tma_kernel(), S::smem);
+            int dev = 0, sms = 0, occ = 0;
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tma_kernel(), S::T, S::smem);
+            if (e == cudaSuccess) resident = sms * (occ > 0 ? occ : 1);
+            return e;
+        } else if constexpr (S::BULK) {
+            if constexpr (S::MINB == 2) return set_smem(k_p3_z_bulk_2b<real, N, S::L, S::T, S::R3>, S::smem);
+            else return set_smem(k_p3_z_bulk<real, N, S::L, S::T, S::R3>, S::smem);
+        } else if constexpr (S::MINB == 2) {
+            return set_smem(k_p3_z_cross_2b<real, N, S::L, S::T, S::R3>, S::smem);
+        } else {
+            return set_smem(k_p3_z_cross<real, N, S::L, S::T, S::R3>, S::smem);
+        }
     }
 };
 

@@ -27,6 +27,7 @@
 //                              P5a writes the transformed N^ here in the state layout
 #pragma once
 
+#include "dns_async.cuh"
 #include "dns_fft.cuh"
 
 namespace dns {
@@ -38,6 +39,7 @@ struct Geo {
     long long sB;  // elements per B field      = N*N*Kzp
     int nb;        // boxes of this size advanced together (batch), >= 1
     long long bS, bA, bB;  // elements between consecutive boxes in the state, A and B
+    int *err;      // device status word: a bounded wait that gave up writes its code here
 };
 
 // Arguments of P5b.  stage in 0..3 performs that RK4 stage; stage = -1 writes
@@ -183,40 +185,22 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
 // fields.  The first inverse stage packs straight from HBM (coalesced along
 // kz); the cross product is computed inside the first forward stage, so the
 // physical values are read once from shared memory and never stored.
+// Forward half of P3, on the tile the inverse half left in natural order
+// (pair p of line l at row p*L + l): u x omega fused into the first forward
+// stage (component order c0 = a1 b2 - a2 b1, c1 = a2 b0 - a0 b2,
+// c2 = a0 b1 - a1 b0; line l becomes Nx + i Ny, line L + l becomes Nz + 0i),
+// the remaining stages, then the two real transforms of line l unpacked and
+// kz <= K stored to fields 0..2 of B (already offset to the box).
 template <typename real, int N, int L, int T, int MAXR>
-__device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__restrict__ twg,
-                                        typename CT<real>::t *__restrict__ B) {
+__device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>::t *tile,
+                                                 const typename CT<real>::t *tw, typename CT<real>::t *B,
+                                                 long long line0) {
     typedef typename CT<real>::t cplx;
     constexpr int LDR = row_ld(N);
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
-    cplx *tile = tw + N;  // [3L][LDR]: pair p of line l at row p*L + l
-    load_twiddles<real>(tw, twg, N);
-    __syncthreads();
     const int K = g.K, Kzp = g.Kzp;
-    const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
-    const long long box = lineg / ((long long)N * N), line0 = lineg % ((long long)N * N);
     const long long sB = g.sB;
-    B += box * g.bB;
-    // ---- inverse: 3 packed lines per physical line, natural order into the tile
-    auto iload = [&](int vl, int n) -> cplx {
-        const int p = vl / L, l = vl % L;
-        const int kz = n <= N / 2 ? n : N - n;
-        if (kz > K) return cmk<cplx>(0.0, 0.0);
-        const long long off = (line0 + l) * Kzp + kz;
-        cplx a = B[(2 * p) * sB + off];
-        cplx b = B[(2 * p + 1) * sB + off];
-        if (kz == 0) {
-            a.y = 0;
-            b.y = 0;
-        }
-        return n <= N / 2 ? cmk<cplx>(a.x - b.y, a.y + b.x) : cmk<cplx>(a.x + b.y, b.x - a.y);
-    };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
-    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
-    // ---- forward, first stage fused with u x omega (component order
-    // c0 = a1 b2 - a2 b1, c1 = a2 b0 - a0 b2, c2 = a0 b1 - a1 b0); line l
-    // becomes Nx + i Ny, line L + l becomes Nz + 0 i
+    auto noload = [&](int, int) -> cplx { return cmk<cplx>(0.0, 0.0); };
     {
         constexpr FftPlan P = make_plan(N, MAXR);
         constexpr int R = P.r[0];
@@ -256,9 +240,8 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
             }
         }
         __syncthreads();
-        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1>::run(tile, tw, iload, tstore);
+        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1>::run(tile, tw, noload, tstore);
     }
-    // ---- unpack the two real transforms of line l and store kz <= K
     for (int e = threadIdx.x; e < L * (K + 1); e += T) {
         const int kz = e % (K + 1), l = e / (K + 1);
         const cplx za = tile[l * LDR + radd(kz)];
@@ -272,6 +255,46 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
     }
 }
 
+// First-stage input of the packed inverse: virtual line vl = p L + l holds
+// field 2p + i field 2p+1 of line l, Hermitian-extended along z (a, b are
+// the two fields' coefficients at kz = n or N - n).
+template <typename cplx>
+__device__ __forceinline__ cplx p3_pack(cplx a, cplx b, int n, int kz, int N) {
+    if (kz == 0) {
+        a.y = 0;
+        b.y = 0;
+    }
+    return n <= N / 2 ? cmk<cplx>(a.x - b.y, a.y + b.x) : cmk<cplx>(a.x + b.y, b.x - a.y);
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                        typename CT<real>::t *__restrict__ B) {
+    typedef typename CT<real>::t cplx;
+    constexpr int LDR = row_ld(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
+    cplx *tile = tw + N;  // [3L][LDR]: pair p of line l at row p*L + l
+    load_twiddles<real>(tw, twg, N);
+    __syncthreads();
+    const int K = g.K, Kzp = g.Kzp;
+    const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
+    const long long box = lineg / ((long long)N * N), line0 = lineg % ((long long)N * N);
+    const long long sB = g.sB;
+    B += box * g.bB;
+    // ---- inverse: 3 packed lines per physical line, natural order into the tile
+    auto iload = [&](int vl, int n) -> cplx {
+        const int p = vl / L, l = vl % L;
+        const int kz = n <= N / 2 ? n : N - n;
+        if (kz > K) return cmk<cplx>(0.0, 0.0);
+        const long long off = (line0 + l) * Kzp + kz;
+        return p3_pack(B[(2 * p) * sB + off], B[(2 * p + 1) * sB + off], n, kz, N);
+    };
+    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
+    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B, line0);
+}
+
 // Two launch-bound flavours of P3 (the autotuner picks): the compiler's own
 // register choice, or a limit that keeps two blocks resident per SM.
 template <typename real, int N, int L, int T, int MAXR>
@@ -283,6 +306,176 @@ template <typename real, int N, int L, int T, int MAXR>
 __global__ void __launch_bounds__(T, 2) k_p3_z_cross_2b(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                         typename CT<real>::t *__restrict__ B) {
     p3_body<real, N, L, T, MAXR>(g, twg, B);
+}
+
+// P3 as a persistent kernel whose line groups arrive by bulk asynchronous
+// copy: each block walks groups blockIdx.x, blockIdx.x + gridDim.x, ...; the
+// six input fields of a group (L consecutive lines, contiguous in B) are
+// copied into a shared staging buffer, and the copy of the next group is
+// issued as soon as the first inverse stage has consumed the current one, so
+// it overlaps the rest of the group's transforms.  Shared memory:
+// twiddles [N] | tile [3L][row_ld(N)] | staging [6][L][Kzp] (16-byte aligned).
+// A copy that does not complete within the wait limit sets g.err and ends
+// the block.
+template <typename real, int N, int L> struct P3Stage {
+    typedef typename CT<real>::t cplx;
+    static constexpr int KZP = ((N - 1) / 3 + 1 + 3) / 4 * 4;
+    static constexpr size_t head = sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
+    static constexpr size_t off = (head + 15) / 16 * 16;
+    static constexpr size_t field_bytes = sizeof(cplx) * (size_t)L * KZP;
+    static constexpr size_t smem = off + 6 * field_bytes;
+};
+
+// Issue the bulk copies of group grp's six input fields (one thread).
+template <typename real, int N, int L>
+__device__ __forceinline__ void p3_issue(const Geo &g, const typename CT<real>::t *B, typename CT<real>::t *stage,
+                                         uint64_t *bar, long long grp) {
+    typedef P3Stage<real, N, L> PS;
+    const long long NN = (long long)N * N, lineg = grp * L;
+    const typename CT<real>::t *src = B + (lineg / NN) * g.bB + (lineg % NN) * PS::KZP;
+    mbar_arrive_expect_tx(bar, (uint32_t)(6 * PS::field_bytes));
+#pragma unroll
+    for (int f = 0; f < 6; ++f)
+        bulk_copy_g2s(stage + f * (L * PS::KZP), src + f * g.sB, (uint32_t)PS::field_bytes, bar);
+}
+
+// One group of L lines from the staging buffer (its copy has landed); issues
+// the copy of group `next` (if >= 0) once the first stage has read the
+// buffer.  Not inlined: inside the group loop the compiler would otherwise
+// hoist the transforms' loop-invariant index arithmetic into registers.
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __noinline__ void p3_tma_group(Geo g, const typename CT<real>::t *tw, typename CT<real>::t *tile,
+                                          typename CT<real>::t *stage, uint64_t *bar,
+                                          typename CT<real>::t *B, long long grp, long long next) {
+    typedef typename CT<real>::t cplx;
+    typedef P3Stage<real, N, L> PS;
+    constexpr int LDR = row_ld(N);
+    const int K = g.K;
+    const long long NN = (long long)N * N;
+    const long long lineg = grp * L;
+    const long long box = lineg / NN, line0 = lineg % NN;
+    auto iload = [&](int vl, int n) -> cplx {
+        const int p = vl / L, l = vl % L;
+        const int kz = n <= N / 2 ? n : N - n;
+        if (kz > K) return cmk<cplx>(0.0, 0.0);
+        const cplx *row = stage + l * PS::KZP + kz;
+        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+    };
+    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, true>::run(tile, tw, iload, tstore);
+    // the staging buffer is free: fetch the next group while this one finishes
+    if (threadIdx.x == 0 && next >= 0) {
+        fence_proxy_async_smem();
+        p3_issue<real, N, L>(g, B, stage, bar, next);
+    }
+    constexpr FftPlan P = make_plan(N, MAXR);
+    if constexpr (P.nst > 1) RowFFT<real, N, 3 * L, T, +1, MAXR, 1>::run(tile, tw, iload, tstore);
+    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_tma_body(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                            typename CT<real>::t *__restrict__ B, long long ngroups) {
+    typedef typename CT<real>::t cplx;
+    typedef P3Stage<real, N, L> PS;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
+    cplx *tile = tw + N;
+    cplx *stage = reinterpret_cast<cplx *>(smem_raw + PS::off);
+    load_twiddles<real>(tw, twg, N);
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    long long grp = blockIdx.x;
+    if (threadIdx.x == 0 && grp < ngroups) p3_issue<real, N, L>(g, B, stage, &bar, grp);
+    uint32_t parity = 0;
+    for (; grp < ngroups; grp += gridDim.x) {
+        if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, parity) ? 1 : 0;
+        // this barrier also orders the previous group's last tile reads
+        // before this group's first-stage writes
+        __syncthreads();
+        if (!s_ok) {
+            if (threadIdx.x == 0) {
+                record_error(g.err, kErrWaitTimeout);
+                mbar_wait_bounded(&bar, parity);  // let the copy in flight land before the block ends
+            }
+            return;
+        }
+        mbar_try_wait(&bar, parity);  // completed: acquire the copied data in every thread
+        parity ^= 1;
+        const long long next = grp + gridDim.x < ngroups ? grp + gridDim.x : -1;
+        p3_tma_group<real, N, L, T, MAXR>(g, tw, tile, stage, &bar, B, grp, next);
+    }
+}
+
+// P3 with one group per block whose input arrives by bulk asynchronous copy
+// into the tile itself (the first inverse stage reads every input value
+// into registers before its barrier, so its writes may overwrite them).
+// Same shared memory as k_p3_z_cross; the copy engine does the loads.
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                             typename CT<real>::t *__restrict__ B) {
+    typedef typename CT<real>::t cplx;
+    typedef P3Stage<real, N, L> PS;
+    constexpr int LDR = row_ld(N);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
+    cplx *tile = tw + N;
+    cplx *stage = tile;  // 16-byte aligned: N complex values precede it
+    const long long grp = blockIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        p3_issue<real, N, L>(g, B, stage, &bar, grp);
+    }
+    load_twiddles<real>(tw, twg, N);
+    if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+        if (threadIdx.x == 0) {
+            record_error(g.err, kErrWaitTimeout);
+            mbar_wait_bounded(&bar, 0);  // let the copy in flight land before the block ends
+        }
+        return;
+    }
+    mbar_try_wait(&bar, 0);  // completed: acquire the copied data in every thread
+    const int K = g.K;
+    const long long NN = (long long)N * N, lineg = grp * L;
+    const long long box = lineg / NN, line0 = lineg % NN;
+    auto iload = [&](int vl, int n) -> cplx {
+        const int p = vl / L, l = vl % L;
+        const int kz = n <= N / 2 ? n : N - n;
+        if (kz > K) return cmk<cplx>(0.0, 0.0);
+        const cplx *row = stage + l * PS::KZP + kz;
+        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+    };
+    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
+    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p3_z_bulk(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                 typename CT<real>::t *__restrict__ B) {
+    p3_bulk_body<real, N, L, T, MAXR>(g, twg, B);
+}
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T, 2) k_p3_z_bulk_2b(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                       typename CT<real>::t *__restrict__ B) {
+    p3_bulk_body<real, N, L, T, MAXR>(g, twg, B);
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p3_z_tma(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                typename CT<real>::t *__restrict__ B, long long ngroups) {
+    p3_tma_body<real, N, L, T, MAXR>(g, twg, B, ngroups);
+}
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T, 2) k_p3_z_tma_2b(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                      typename CT<real>::t *__restrict__ B, long long ngroups) {
+    p3_tma_body<real, N, L, T, MAXR>(g, twg, B, ngroups);
 }
 
 // ------------------------------------------------------------------- physical input
