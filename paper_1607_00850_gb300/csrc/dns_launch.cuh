@@ -49,10 +49,13 @@ __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
 }
 __host__ __device__ constexpr int at_least_32(int t) { return t < 32 ? 32 : t; }
 
+// Column variants 0..2 load their input with the threads; 3..5 are the same
+// shapes fed by bulk copies of the tile's input rows.
 template <typename real, int N, int V> struct ColShape {
     typedef VariantTable<real> VT;
-    static constexpr int W = VT::colW[V];
-    static constexpr int RC = VT::colR[V];
+    static constexpr int W = VT::colW[V % 3];
+    static constexpr int RC = VT::colR[V % 3];
+    static constexpr bool BULK = V >= 3;
     static constexpr int T = at_least_32(raw_threads(N, W, VT::BUD));
     typedef typename CT<real>::t cplx;
     static constexpr size_t smem = sizeof(cplx) * (size_t)(N + N * W);
@@ -110,34 +113,34 @@ template <typename real, int N, int V> struct ColLaunch {
     static cudaError_t p1(const Geo &g, const void *tw, const void *U, const void *Om, void *A, double scale,
                           cudaStream_t st) {
         dim3 grid(6 * g.nb, cdiv(g.Kz, S::W), g.Kx);
-        k_p1_xinv<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(
+        k_p1_xinv<real, N, S::W, S::T, S::RC, S::BULK><<<grid, S::T, S::smem, st>>>(
             g, (const cplx *)tw, (const cplx *)U, (const cplx *)Om, (cplx *)A, (real)scale);
         return cudaGetLastError();
     }
     static cudaError_t p2(const Geo &g, const void *tw, const void *A, void *B, cudaStream_t st) {
         dim3 grid(cdiv(g.Kz, S::W), N, 6 * g.nb);
-        k_p2_yinv<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)A,
+        k_p2_yinv<real, N, S::W, S::T, S::RC, S::BULK><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)A,
                                                                            (cplx *)B);
         return cudaGetLastError();
     }
     static cudaError_t p4(const Geo &g, const void *tw, const void *B, void *A, cudaStream_t st) {
         dim3 grid(cdiv(g.Kz, S::W), N, 3 * g.nb);
-        k_p4_yfwd<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)B,
+        k_p4_yfwd<real, N, S::W, S::T, S::RC, S::BULK><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (const cplx *)B,
                                                                            (cplx *)A);
         return cudaGetLastError();
     }
     static cudaError_t p5a(const Geo &g, const void *tw, const void *A, void *Nh, cudaStream_t st) {
         dim3 grid(3 * g.nb, cdiv(g.Kz, S::W), g.Kx);
-        k_p5a_xfwd<real, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
+        k_p5a_xfwd<real, N, S::W, S::T, S::RC, S::BULK><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
                                                                             (const cplx *)A, (cplx *)Nh);
         return cudaGetLastError();
     }
     static cudaError_t prepare() {
         cudaError_t e;
-        if ((e = set_smem(k_p1_xinv<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
-        if ((e = set_smem(k_p2_yinv<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
-        if ((e = set_smem(k_p4_yfwd<real, N, S::W, S::T, S::RC>, S::smem)) != cudaSuccess) return e;
-        return set_smem(k_p5a_xfwd<real, N, S::W, S::T, S::RC>, S::smem);
+        if ((e = set_smem(k_p1_xinv<real, N, S::W, S::T, S::RC, S::BULK>, S::smem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_p2_yinv<real, N, S::W, S::T, S::RC, S::BULK>, S::smem)) != cudaSuccess) return e;
+        if ((e = set_smem(k_p4_yfwd<real, N, S::W, S::T, S::RC, S::BULK>, S::smem)) != cudaSuccess) return e;
+        return set_smem(k_p5a_xfwd<real, N, S::W, S::T, S::RC, S::BULK>, S::smem);
     }
 };
 

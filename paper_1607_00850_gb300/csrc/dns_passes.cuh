@@ -80,29 +80,71 @@ template <typename real> __device__ __forceinline__ void load_twiddles(typename 
     for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
 }
 
+// ------------------------------------------------------------------- bulk-fed column tiles
+// Rows [0, nrows) of a column tile (row r: ncols complex values at
+// src + r * stride, 16-byte aligned, ncols * sizeof(cplx) a multiple of 16)
+// copied by the bulk copy engine to stage[r * W ...].  rows_issue is called
+// by every thread (thread 0 arms the barrier, then each thread issues rows
+// tid, tid + T, ...); rows_wait waits (bounded, one thread) and returns false
+// after recording the timeout, in which case the block must return.
+template <typename cplx, int W>
+__device__ __forceinline__ void rows_issue(cplx *stage, const cplx *src, long long stride, int nrows, int ncols,
+                                           uint64_t *bar) {
+    const uint32_t rb = (uint32_t)(ncols * sizeof(cplx));
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_arrive_expect_tx(bar, rb * (uint32_t)nrows);
+    }
+    __syncthreads();
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) bulk_copy_g2s(stage + r * W, src + r * stride, rb, bar);
+}
+
+__device__ __forceinline__ bool rows_wait(uint64_t *bar, int *s_ok, int *err) {
+    if (threadIdx.x == 0) *s_ok = mbar_wait_bounded(bar, 0) ? 1 : 0;
+    __syncthreads();
+    if (!*s_ok) {
+        if (threadIdx.x == 0) {
+            record_error(err, kErrWaitTimeout);
+            mbar_wait_bounded(bar, 0);  // let the copies in flight land before the block ends
+        }
+        return false;
+    }
+    mbar_try_wait(bar, 0);  // completed: acquire the copied data in every thread
+    return true;
+}
+
 // ------------------------------------------------------------------- P1
 // Inverse transform along x of u (fields 0..2, from U) and of omega^ = i k x
 // uhat (fields 3..5, from Om, written by the previous update or by k_curl).
-template <typename real, int N, int W, int T, int MAXR>
+// BULK: the Kx input rows of the tile arrive by bulk copy into the tile
+// itself (the first stage reads all its inputs before its barrier).
+template <typename real, int N, int W, int T, int MAXR, bool BULK>
 __global__ void __launch_bounds__(T) k_p1_xinv(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                const typename CT<real>::t *__restrict__ U,
                                                const typename CT<real>::t *__restrict__ Om,
                                                typename CT<real>::t *__restrict__ A, real scale) {
     typedef typename CT<real>::t cplx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
-    __syncthreads();
     const int box = blockIdx.x / 6, f = blockIdx.x % 6, kz0 = blockIdx.y * W, jy = blockIdx.z;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const cplx *src = (f < 3 ? U + f * g.sS : Om + (f - 3) * g.sS) + box * g.bS + (long long)jy * Kzp;
     cplx *dst = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
+    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, Kx, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) {
+        if (!rows_wait(&bar, &s_ok, g.err)) return;
+    } else {
+        __syncthreads();
+    }
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         const int ix = row_to_compact<N>(n, K);
         if (kz >= Kz || ix < 0) return cmk<cplx>(0.0, 0.0);
-        const cplx v = src[(long long)ix * Kx * Kzp + kz];
+        const cplx v = BULK ? tile[ix * W + c] : src[(long long)ix * Kx * Kzp + kz];
         return cmk<cplx>(v.x * scale, v.y * scale);
     };
     auto store = [&](int n, int c, cplx v) {
@@ -146,20 +188,27 @@ __global__ void k_curl(Geo g, const typename CT<real>::t *__restrict__ U, typena
 }
 
 // ------------------------------------------------------------------- P2
-template <typename real, int N, int W, int T, int MAXR>
+template <typename real, int N, int W, int T, int MAXR, bool BULK>
 __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                const typename CT<real>::t *__restrict__ A,
                                                typename CT<real>::t *__restrict__ B) {
     typedef typename CT<real>::t cplx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
-    __syncthreads();
     const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 6, f = blockIdx.z % 6;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const cplx *src = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
     cplx *dst = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
+    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, Kx, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) {
+        if (!rows_wait(&bar, &s_ok, g.err)) return;
+    } else {
+        __syncthreads();
+    }
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         const int iy = row_to_compact<N>(n, K);
@@ -167,7 +216,7 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
         z.x = 0;
         z.y = 0;
         if (kz >= Kz || iy < 0) return z;
-        return src[(long long)iy * Kzp + kz];
+        return BULK ? tile[iy * W + c] : src[(long long)iy * Kzp + kz];
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
@@ -518,24 +567,31 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
 }
 
 // ------------------------------------------------------------------- P4
-template <typename real, int N, int W, int T, int MAXR>
+template <typename real, int N, int W, int T, int MAXR, bool BULK>
 __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                const typename CT<real>::t *__restrict__ B,
                                                typename CT<real>::t *__restrict__ A) {
     typedef typename CT<real>::t cplx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
-    __syncthreads();
     const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 3, f = blockIdx.z % 3;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const cplx *src = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
     cplx *dst = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
+    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, N, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) {
+        if (!rows_wait(&bar, &s_ok, g.err)) return;
+    } else {
+        __syncthreads();
+    }
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
-        return src[(long long)n * Kzp + kz];
+        return BULK ? tile[n * W + c] : src[(long long)n * Kzp + kz];
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
@@ -630,24 +686,31 @@ __device__ __forceinline__ typename CT<real>::t rk_update_if(const UpdateArgs<re
 
 // P5a: forward transform along x of the 3 fields, keep the Kx stored rows;
 // the result N^ (dealiased by construction) goes to a compact buffer.
-template <typename real, int N, int W, int T, int MAXR>
+template <typename real, int N, int W, int T, int MAXR, bool BULK>
 __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::t *__restrict__ twg,
                                                 const typename CT<real>::t *__restrict__ A,
                                                 typename CT<real>::t *__restrict__ Nh) {
     typedef typename CT<real>::t cplx;
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
-    __syncthreads();
     const int box = blockIdx.x / 3, f = blockIdx.x % 3, kz0 = blockIdx.y * W, jy = blockIdx.z;
     const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const cplx *src = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
     cplx *dst = Nh + box * g.bB + f * g.sS + (long long)jy * Kzp;
+    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, N, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) {
+        if (!rows_wait(&bar, &s_ok, g.err)) return;
+    } else {
+        __syncthreads();
+    }
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
-        return src[(long long)n * Kx * Kzp + kz];
+        return BULK ? tile[n * W + c] : src[(long long)n * Kx * Kzp + kz];
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
