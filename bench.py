@@ -41,6 +41,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64", action="store_true")
     p.add_argument("--no-ensemble", action="store_true")
+    p.add_argument("--no-les", action="store_true")
     p.add_argument("--plan", default=None,
                    help="five comma-separated pass variants; skips the autotuner (profiling runs)")
     return p.parse_args()
@@ -60,7 +61,7 @@ def config(N, dt):
             "l2": "inputs larger than L2 (working set several GB); no flush"}
 
 
-KERNEL_SOURCES = ("dns_fft.cuh", "dns_passes.cuh", "dns_launch.cuh", "dns_inst.cu")
+KERNEL_SOURCES = ("dns_fft.cuh", "dns_async.cuh", "dns_passes.cuh", "dns_launch.cuh", "dns_inst.cu")
 
 
 def kernel_source_hash():
@@ -351,6 +352,8 @@ def run_ours(args, rank, world, local_rank):
     del uh
     if not args.no_ensemble:
         extra["ensemble"] = ensemble_bench(args, stream)
+    if not args.no_les:
+        extra["les_closure"] = les_closure_bench()
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -398,6 +401,28 @@ def ensemble_bench(args, stream):
             "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
             "step_frac_216F_model": sum(survey_step_bytes(n, 0) for n in Ns) / (ms / args.steps / 1e3) / 1e9 / peak,
             "peak_source": src, "energy_min": float(E.min()), "energy_max": float(E.max())}
+
+
+def bf16_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["bf16_tflops"]), "measured"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def les_closure_bench():
+    """The learned LES closure at 64^3 (9 -> 32 -> 32 -> 6 periodic 3^3
+    convolutions, BF16 tensor-core MMA with FP32 accumulation): forward
+    TFLOP/s against the dense BF16 peak, training step per sample, LES step
+    costs, next to a 256^3 DNS step."""
+    from paper_1607_00850_gb300 import experiments
+    r = experiments.les_bench(64)
+    peak, src = bf16_peak()
+    r["roofline"] = {"bound": "tensor", "kernel": "k_conv (three layers)", "achieved": r["forward_tflops"],
+                     "peak": peak, "unit": "TFLOP/s", "frac": r["forward_tflops"] / peak, "peak_source": src}
+    return r
 
 
 def cpu_baseline(N, nu):

@@ -184,6 +184,26 @@ static dns::UpdateArgsErased stage_args(const dns_ctx *h, int s) {
     return a;
 }
 
+// The back end of a stage: forward x transform and update, either as P5a +
+// P5b or fused (plan[4] >= NCOLV); `mark` runs after each of the two slots
+// (after the fused launch and again with nothing in between).
+template <class Mark>
+static cudaError_t launch_back(dns_ctx *h, const Geo &g, const dns::UpdateArgsErased &a, const Mark &mark) {
+    cudaError_t e;
+    const int v = h->plan[4];
+    if (v >= dns::PassSet::NCOLV) {
+        if ((e = h->ps.p5f[v - dns::PassSet::NCOLV](g, h->tw, h->A, a, h->stream)) != cudaSuccess) return e;
+        if ((e = mark()) != cudaSuccess) return e;
+        return mark();
+    }
+    if ((e = h->ps.p5a[v](g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
+    if ((e = mark()) != cudaSuccess) return e;
+    if ((e = h->ps.p5b(g, h->B, a, h->stream)) != cudaSuccess) return e;
+    return mark();
+}
+
+static cudaError_t no_mark() { return cudaSuccess; }
+
 // Enqueue one RK4 step; if ev != nullptr record ev[1 + i] after launch i.
 static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
     cudaError_t e;
@@ -206,10 +226,7 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
         if ((e = mark()) != cudaSuccess) return e;
         if ((e = h->ps.p4[h->plan[3]](h->g, h->tw, h->B, h->A, h->stream)) != cudaSuccess) return e;
         if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream)) != cudaSuccess) return e;
-        if ((e = mark()) != cudaSuccess) return e;
-        if ((e = h->ps.p5b(h->g, h->B, a, h->stream)) != cudaSuccess) return e;
-        if ((e = mark()) != cudaSuccess) return e;
+        if ((e = launch_back(h, h->g, a, mark)) != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
@@ -373,6 +390,8 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
         if (h->ps.prep_col[v]) e = h->ps.prep_col[v]();
     for (int v = 0; v < dns::PassSet::NP3V && e == cudaSuccess; ++v)
         if (h->ps.prep_p3[v]) e = h->ps.prep_p3[v]();
+    for (int v = 0; v < dns::PassSet::NP5F && e == cudaSuccess; ++v)
+        if (h->ps.prep_p5f[v]) e = h->ps.prep_p5f[v]();
     if (e == cudaSuccess) e = h->ps.prep_misc();
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
     if (e != cudaSuccess) {
@@ -448,8 +467,7 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
     dns::UpdateArgsErased a{};
     a.dU = h->rout;
     a.stage = -2;
-    CK(h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream));
-    CK(h->ps.p5b(h->g, h->B, a, h->stream));
+    CK(launch_back(h, h->g, a, no_mark));
     const long long n = 3 * h->g.sS;
     CK(cudaMemcpyAsync(h->U0, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
     if (h->same_type) {
@@ -490,8 +508,7 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
         CK(dns::les_closure_forcing(h->closure, h->g, h->rin, h->Fext, h->stream));
         a.Fext = h->Fext;
     }
-    CK(h->ps.p5a[h->plan[4]](h->g, h->tw, h->A, h->B, h->stream));
-    CK(h->ps.p5b(h->g, h->B, a, h->stream));
+    CK(launch_back(h, h->g, a, no_mark));
     if (on_device) {
         CK(acc_to_full(h, h->rout, duhat_out));
     } else {
@@ -649,25 +666,49 @@ static void drop_graph(dns_ctx *h) {
 static bool variant_exists(const dns_ctx *h, int pass, int v) {
     if (pass == 2) return v >= 0 && v < dns::PassSet::NP3V && h->ps.p3[v];
     if (pass < 0 || pass > 4) return false;
+    if (pass == 4 && v >= dns::PassSet::NCOLV)
+        return v < dns::PassSet::NCOLV + dns::PassSet::NP5F && h->ps.p5f[v - dns::PassSet::NCOLV];
     return v >= 0 && v < dns::PassSet::NCOLV && h->ps.p1[v];
 }
 
-static int variant_count(int pass) { return pass == 2 ? dns::PassSet::NP3V : dns::PassSet::NCOLV; }
+static int variant_count(int pass) {
+    if (pass == 2) return dns::PassSet::NP3V;
+    return pass == 4 ? dns::PassSet::NCOLV + dns::PassSet::NP5F : dns::PassSet::NCOLV;
+}
 
 // Mean device time of `reps` launches of one variant of one pass on the
-// handle's scratch buffers (A, B); the state is only read.
+// handle's scratch buffers; the state is only read.  Pass 4 is timed
+// together with the update it feeds (P5a + P5b, or the fused form) as a
+// middle RK4 stage of the first box (the heaviest stage: it reads u, u0, u1
+// and writes u1, the next input and its curl), with those three outputs
+// redirected to the right-hand-side scratch buffers, so both forms compare
+// on the work a step does.
 static cudaError_t time_variant(dns_ctx *h, int pass, int v, int reps, float *ms) {
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     cudaError_t e = cudaEventCreate(&e0);
     if (e == cudaSuccess) e = cudaEventCreate(&e1);
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
+    Geo g1 = h->g;
+    g1.nb = 1;
+    dns::UpdateArgsErased ra = stage_args(h, 1);
+    ra.U = h->U;
+    ra.U1 = h->rout;   // accumulator type, 3 fields of one box
+    ra.Uout = h->rin;  // field type
+    ra.Om = h->rom;    // field type
+    ra.Fext = nullptr;
+    ra.nu_box = nullptr;
     auto launch = [&]() -> cudaError_t {
         switch (pass) {
             case 0: return h->ps.p1[v](h->g, h->tw, h->U, h->Om, h->A, scale, h->stream);
             case 1: return h->ps.p2[v](h->g, h->tw, h->A, h->B, h->stream);
             case 2: return h->ps.p3[v](h->g, h->tw, h->B, h->stream);
             case 3: return h->ps.p4[v](h->g, h->tw, h->B, h->A, h->stream);
-            default: return h->ps.p5a[v](h->g, h->tw, h->A, h->B, h->stream);
+            default: {
+                if (v >= dns::PassSet::NCOLV)
+                    return h->ps.p5f[v - dns::PassSet::NCOLV](g1, h->tw, h->A, ra, h->stream);
+                cudaError_t e2 = h->ps.p5a[v](g1, h->tw, h->A, h->B, h->stream);
+                return e2 != cudaSuccess ? e2 : h->ps.p5b(g1, h->B, ra, h->stream);
+            }
         }
     };
     if (e == cudaSuccess) e = launch();  // warm-up
@@ -807,6 +848,11 @@ int dns_variant_info(dns_handle h, int pass, int variant, int *lines, int *max_r
         if (lines) *lines = h->ps.p3_l[variant];
         if (max_radix) *max_radix = h->ps.p3_r[variant];
         if (threads) *threads = h->ps.p3_t[variant];
+    } else if (pass == 4 && variant >= dns::PassSet::NCOLV) {
+        const int f = variant - dns::PassSet::NCOLV;
+        if (lines) *lines = h->ps.p5f_w[f];
+        if (max_radix) *max_radix = h->ps.p5f_r[f];
+        if (threads) *threads = h->ps.p5f_t[f];
     } else {
         if (lines) *lines = h->ps.col_w[variant];
         if (max_radix) *max_radix = h->ps.col_r[variant];

@@ -25,6 +25,7 @@ typedef cudaError_t (*ColP1)(const Geo &, const void *tw, const void *U, const v
 typedef cudaError_t (*ColPass)(const Geo &, const void *tw, const void *src, void *dst, cudaStream_t);
 typedef cudaError_t (*ZPass)(const Geo &, const void *tw, void *B, cudaStream_t);
 typedef cudaError_t (*Prep)();
+typedef cudaError_t (*P5Fused)(const Geo &, const void *tw, const void *A, const UpdateArgsErased &, cudaStream_t);
 
 // Entry points for one (N, dtype): every compiled variant of each tuned pass
 // (nullptr where a shape is not compiled) and the untuned kernels.
@@ -39,6 +40,11 @@ struct PassSet {
     Prep prep_p3[NP3V] = {};
     int p3_l[NP3V] = {}, p3_r[NP3V] = {}, p3_t[NP3V] = {};
     cudaError_t (*p5b)(const Geo &, const void *Nh, const UpdateArgsErased &, cudaStream_t) = nullptr;
+    // fused P5a + P5b variants; plan[4] = NCOLV + v selects p5f[v]
+    static constexpr int NP5F = 2;
+    P5Fused p5f[NP5F] = {};
+    Prep prep_p5f[NP5F] = {};
+    int p5f_w[NP5F] = {}, p5f_r[NP5F] = {}, p5f_t[NP5F] = {};
     // physical real lines [3][N][N][N] (io real type) -> B fields 0..2, kz <= K
     cudaError_t (*zfwd)(const Geo &, const void *tw, const void *u, void *B, cudaStream_t) = nullptr;
     // Om = i k x U on the stored modes (all boxes of the context)

@@ -224,7 +224,7 @@ template <typename real, int N> struct MiscLaunch {
 template <typename real, typename acc> struct UpdLaunch {
     typedef typename CT<real>::t cplx;
     typedef typename CT<acc>::t cacc;
-    static cudaError_t p5b(const Geo &g, const void *Nh, const UpdateArgsErased &e, cudaStream_t st) {
+    static UpdateArgs<real, acc> args(const UpdateArgsErased &e) {
         UpdateArgs<real, acc> a;
         a.U = (const cplx *)e.U;
         a.U0 = (const cacc *)e.U0;
@@ -241,11 +241,50 @@ template <typename real, typename acc> struct UpdLaunch {
         a.stage = e.stage;
         a.dt = e.dt;
         a.ifrk = e.ifrk;
+        return a;
+    }
+    static cudaError_t p5b(const Geo &g, const void *Nh, const UpdateArgsErased &e, cudaStream_t st) {
         const long long n = g.sS * g.nb;
         const unsigned blocks = (unsigned)((n + 255) / 256);
-        k_p5b_update<real, acc><<<blocks, 256, 0, st>>>(g, (const cplx *)Nh, a);
+        k_p5b_update<real, acc><<<blocks, 256, 0, st>>>(g, (const cplx *)Nh, args(e));
         return cudaGetLastError();
     }
+};
+
+// Fused x-forward + update (P5a + P5b): W columns of each of the three
+// fields per block, radix cap RC.
+template <typename real> struct FusedTable;
+// BUD: complex values a thread holds per stage (sets the thread count).
+template <> struct FusedTable<float> {
+    static constexpr int W[2] = {8, 8};
+    static constexpr int R[2] = {16, 16};
+    static constexpr int BUD[2] = {32, 16};
+};
+template <> struct FusedTable<double> {
+    static constexpr int W[2] = {4, 4};
+    static constexpr int R[2] = {8, 8};
+    static constexpr int BUD[2] = {16, 8};
+};
+
+template <typename real, int N, int V> struct FusedShape {
+    static constexpr int W = FusedTable<real>::W[V];
+    static constexpr int RC = FusedTable<real>::R[V];
+    static constexpr int T = at_least_32(raw_threads(N, 3 * W, FusedTable<real>::BUD[V]));
+    typedef typename CT<real>::t cplx;
+    static constexpr size_t smem = sizeof(cplx) * (size_t)(N + 3 * N * W);
+    static constexpr bool valid = N >= 64 && T <= 1024 && smem <= kMaxSmem;
+};
+
+template <typename real, typename acc, int N, int V> struct FusedLaunch {
+    typedef FusedShape<real, N, V> S;
+    typedef typename CT<real>::t cplx;
+    static cudaError_t p5f(const Geo &g, const void *tw, const void *A, const UpdateArgsErased &e, cudaStream_t st) {
+        dim3 grid(g.nb, cdiv(g.Kz, S::W), g.Kx);
+        k_p5_fused<real, acc, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(
+            g, (const cplx *)tw, (const cplx *)A, UpdLaunch<real, acc>::args(e));
+        return cudaGetLastError();
+    }
+    static cudaError_t prepare() { return set_smem(k_p5_fused<real, acc, N, S::W, S::T, S::RC>, S::smem); }
 };
 
 // ------------------------------------------------------------------ tables
@@ -280,6 +319,20 @@ template <typename real, int N, int V> static void fill_p3(PassSet *ps) {
     }
 }
 
+template <typename real, typename acc, int N, int V> static void fill_p5f(PassSet *ps) {
+    if constexpr (V < PassSet::NP5F) {
+        typedef FusedShape<real, N, V> S;
+        if constexpr (S::valid) {
+            ps->p5f[V] = FusedLaunch<real, acc, N, V>::p5f;
+            ps->prep_p5f[V] = FusedLaunch<real, acc, N, V>::prepare;
+            ps->p5f_w[V] = S::W;
+            ps->p5f_r[V] = S::RC;
+            ps->p5f_t[V] = S::T;
+        }
+        fill_p5f<real, acc, N, V + 1>(ps);
+    }
+}
+
 template <int N> bool fill_passes(int dtype, PassSet *ps) {
     *ps = PassSet();
     if (dtype == 1) {
@@ -287,6 +340,7 @@ template <int N> bool fill_passes(int dtype, PassSet *ps) {
         fill_p3<double, N, 0>(ps);
         ps->curl = MiscLaunch<double, N>::curl;
         ps->p5b = UpdLaunch<double, double>::p5b;
+        fill_p5f<double, double, N, 0>(ps);
         ps->zfwd = MiscLaunch<double, N>::template zfwd<double>;
         ps->prep_misc = MiscLaunch<double, N>::template prepare<double>;
         return true;
@@ -297,10 +351,12 @@ template <int N> bool fill_passes(int dtype, PassSet *ps) {
         ps->curl = MiscLaunch<float, N>::curl;
         if (dtype == 0) {
             ps->p5b = UpdLaunch<float, float>::p5b;
+            fill_p5f<float, float, N, 0>(ps);
             ps->zfwd = MiscLaunch<float, N>::template zfwd<float>;
             ps->prep_misc = MiscLaunch<float, N>::template prepare<float>;
         } else {
             ps->p5b = UpdLaunch<float, double>::p5b;
+            fill_p5f<float, double, N, 0>(ps);
             ps->zfwd = MiscLaunch<float, N>::template zfwd<double>;
             ps->prep_misc = MiscLaunch<float, N>::template prepare<double>;
         }

@@ -92,63 +92,122 @@ __device__ __forceinline__ long long nbr(int n, int x, int y, int z, int t) {
 
 enum { EPI_HIDDEN = 0, EPI_OUT = 1, EPI_DGRAD = 2 };
 
-// Y[v][o] = b[o] + sum_{t,c} X[v + off(t)][c] W[o][t][c], one warp per 16
-// voxels along z, all COUT outputs.  Epilogues:
+// Y[v][o] = b[o] + sum_{t,c} X[v + off(t)][c] W[o][t][c].  A block of 4
+// warps stages the layer's weights in shared memory once (rows padded by 8
+// BF16 so the B-fragment reads of a warp hit 32 distinct banks); each warp
+// computes MT m-tiles of 16 voxels along z (an m-tile never crosses a z
+// line: n % 16 == 0) for all COUT outputs, so one B fragment feeds MT MMAs
+// and one A fragment NT MMAs.  Epilogues:
 //   EPI_HIDDEN: Z = Y (float) and A = bf16(gelu(Z));  EPI_OUT: Z = Y;
 //   EPI_DGRAD:  A = bf16(Y * gelu'(Zp)) (Y is dL/da of the layer below).
+constexpr int CONV_MT = 4;
+constexpr int CONV_VOX = 4 * CONV_MT * 16;  // voxels per block
+
+template <int CIN> __host__ __device__ constexpr int conv_ldw() { return 27 * CIN + 8; }
+template <int CIN, int COUT> constexpr size_t conv_smem() { return sizeof(__nv_bfloat16) * COUT * conv_ldw<CIN>(); }
+
 template <int CIN, int COUT, int EPI>
 __global__ void __launch_bounds__(128) k_conv(int n, const __nv_bfloat16 *__restrict__ X,
                                               const __nv_bfloat16 *__restrict__ W, const float *__restrict__ bias,
                                               float *__restrict__ Z, __nv_bfloat16 *__restrict__ A,
                                               const float *__restrict__ Zp) {
-    constexpr int NT = COUT / 8;
+    constexpr int NT = COUT / 8, MT = CONV_MT, LDW = conv_ldw<CIN>();
+    constexpr int ROW16 = 27 * CIN * 2 / 16;  // 16-byte chunks per weight row
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __nv_bfloat16 *sW = reinterpret_cast<__nv_bfloat16 *>(smem_raw);
+    for (int e = threadIdx.x; e < COUT * ROW16; e += blockDim.x) {
+        const int o = e / ROW16, q = e % ROW16;
+        reinterpret_cast<uint4 *>(sW + o * LDW)[q] = reinterpret_cast<const uint4 *>(W + (long long)o * 27 * CIN)[q];
+    }
+    __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane >> 2, tg = lane & 3;
-    const long long v0 = ((long long)blockIdx.x * 4 + warp) * 16;  // 16 voxels along z
     const long long V = (long long)n * n * n;
+    const long long v0 = ((long long)blockIdx.x * 4 + warp) * (MT * 16);
     if (v0 >= V) return;
-    const int z0 = (int)(v0 % n), y = (int)((v0 / n) % n), x = (int)(v0 / ((long long)n * n));
-    float acc[NT][4];
+    int zb[MT], yb[MT], xb[MT];
 #pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
+    for (int m = 0; m < MT; ++m) {
+        const long long vb = v0 + 16 * m;
+        zb[m] = (int)(vb % n);
+        yb[m] = (int)((vb / n) % n);
+        xb[m] = (int)(vb / ((long long)n * n));
+    }
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int m = 0; m < MT; ++m)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) acc[m][j][0] = acc[m][j][1] = acc[m][j][2] = acc[m][j][3] = 0.f;
     for (int t = 0; t < 27; ++t) {
-        const long long r0 = nbr(n, x, y, z0 + g, t), r1 = nbr(n, x, y, z0 + g + 8, t);
-        const __nv_bfloat16 *xa = X + r0 * CIN, *xb = X + r1 * CIN;
+        const __nv_bfloat16 *xa[MT], *xbp[MT];
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            xa[m] = X + nbr(n, xb[m], yb[m], zb[m] + g, t) * CIN;
+            xbp[m] = X + nbr(n, xb[m], yb[m], zb[m] + g + 8, t) * CIN;
+        }
 #pragma unroll
         for (int kc = 0; kc < CIN; kc += 16) {
-            const uint32_t a0 = ld_b32(xa + kc + 2 * tg), a1 = ld_b32(xb + kc + 2 * tg);
-            const uint32_t a2 = ld_b32(xa + kc + 8 + 2 * tg), a3 = ld_b32(xb + kc + 8 + 2 * tg);
+            uint32_t a[MT][4];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                a[m][0] = ld_b32(xa[m] + kc + 2 * tg);
+                a[m][1] = ld_b32(xbp[m] + kc + 2 * tg);
+                a[m][2] = ld_b32(xa[m] + kc + 8 + 2 * tg);
+                a[m][3] = ld_b32(xbp[m] + kc + 8 + 2 * tg);
+            }
 #pragma unroll
             for (int j = 0; j < NT; ++j) {
-                const __nv_bfloat16 *w = W + ((long long)(j * 8 + g) * 27 + t) * CIN + kc + 2 * tg;
-                mma_bf16(acc[j], a0, a1, a2, a3, ld_b32(w), ld_b32(w + 8));
+                const __nv_bfloat16 *w = sW + (j * 8 + g) * LDW + t * CIN + kc + 2 * tg;
+                const uint32_t b0 = ld_b32(w), b1 = ld_b32(w + 8);
+#pragma unroll
+                for (int m = 0; m < MT; ++m) mma_bf16(acc[m][j], a[m][0], a[m][1], a[m][2], a[m][3], b0, b1);
             }
         }
     }
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
+    for (int m = 0; m < MT; ++m) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const long long v = v0 + g + 8 * h;
-            const int o = j * 8 + 2 * tg;
-            float y0 = acc[j][2 * h], y1 = acc[j][2 * h + 1];
-            if (bias) {
-                y0 += bias[o];
-                y1 += bias[o + 1];
-            }
-            if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
-                Z[v * COUT + o] = y0;
-                Z[v * COUT + o + 1] = y1;
-            }
-            if constexpr (EPI == EPI_HIDDEN) {
-                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(gelu_f(y0), gelu_f(y1));
-            }
-            if constexpr (EPI == EPI_DGRAD) {
-                const float d0 = y0 * gelu_d(Zp[v * COUT + o]), d1 = y1 * gelu_d(Zp[v * COUT + o + 1]);
-                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(d0, d1);
+        for (int j = 0; j < NT; ++j) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const long long v = v0 + 16 * m + g + 8 * h;
+                const int o = j * 8 + 2 * tg;
+                float y0 = acc[m][j][2 * h], y1 = acc[m][j][2 * h + 1];
+                if (bias) {
+                    y0 += bias[o];
+                    y1 += bias[o + 1];
+                }
+                if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
+                    Z[v * COUT + o] = y0;
+                    Z[v * COUT + o + 1] = y1;
+                }
+                if constexpr (EPI == EPI_HIDDEN) {
+                    *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
+                        __floats2bfloat162_rn(gelu_f(y0), gelu_f(y1));
+                }
+                if constexpr (EPI == EPI_DGRAD) {
+                    const float d0 = y0 * gelu_d(Zp[v * COUT + o]), d1 = y1 * gelu_d(Zp[v * COUT + o + 1]);
+                    *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(d0, d1);
+                }
             }
         }
     }
+}
+
+// Launch of one convolution layer (V / CONV_VOX blocks; V is a multiple of
+// CONV_VOX for every supported n).
+template <int CIN, int COUT, int EPI>
+static cudaError_t conv(int n, const __nv_bfloat16 *X, const __nv_bfloat16 *W, const float *bias, float *Z,
+                        __nv_bfloat16 *A, const float *Zp, cudaStream_t st) {
+    const long long V = (long long)n * n * n;
+    k_conv<CIN, COUT, EPI><<<(unsigned)((V + CONV_VOX - 1) / CONV_VOX), 128, conv_smem<CIN, COUT>(), st>>>(
+        n, X, W, bias, Z, A, Zp);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int EPI> static cudaError_t conv_attr() {
+    return cudaFuncSetAttribute(k_conv<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)conv_smem<CIN, COUT>());
 }
 
 // Weight gradient partials: block (chunk, tap) accumulates
@@ -389,12 +448,10 @@ static cudaError_t net_pack(dns_net_ctx *c) {
 
 // forward of one sample already in X0; leaves Z1, A1, Z2, A2, Y3
 static cudaError_t net_forward_x0(dns_net_ctx *c, cudaStream_t st) {
-    const long long V = (long long)c->n * c->n * c->n;
-    const unsigned blocks = (unsigned)((V / 16 + 3) / 4);
-    k_conv<16, 32, EPI_HIDDEN><<<blocks, 128, 0, st>>>(c->n, c->X0, c->W1, c->p + OFF_B1, c->Z1, c->A1, nullptr);
-    k_conv<32, 32, EPI_HIDDEN><<<blocks, 128, 0, st>>>(c->n, c->A1, c->W2, c->p + OFF_B2, c->Z2, c->A2, nullptr);
-    k_conv<32, OUTP, EPI_OUT><<<blocks, 128, 0, st>>>(c->n, c->A2, c->W3, nullptr, c->Y3, nullptr, nullptr);
-    return cudaGetLastError();
+    cudaError_t e = conv<16, 32, EPI_HIDDEN>(c->n, c->X0, c->W1, c->p + OFF_B1, c->Z1, c->A1, nullptr, st);
+    if (e == cudaSuccess) e = conv<32, 32, EPI_HIDDEN>(c->n, c->A1, c->W2, c->p + OFF_B2, c->Z2, c->A2, nullptr, st);
+    if (e == cudaSuccess) e = conv<32, OUTP, EPI_OUT>(c->n, c->A2, c->W3, nullptr, c->Y3, nullptr, nullptr, st);
+    return e;
 }
 
 __global__ void k_scale(float *g, int n, float s) {
@@ -420,8 +477,8 @@ static cudaError_t net_forward(dns_net_ctx *c, const float *g, cudaStream_t st) 
 // backward of the sample in flight (after net_forward), accumulating gradients
 static cudaError_t net_backward(dns_net_ctx *c, const float *tau) {
     const long long V = (long long)c->n * c->n * c->n;
-    const unsigned blocks = (unsigned)((V / 16 + 3) / 4);
     const int lblocks = 256;
+    cudaError_t e;
     k_mse<<<lblocks, 256, 0, c->stream>>>(c->Y3, tau, V, c->dY3, c->lpart);
     k_sum_d<<<1, 32, 0, c->stream>>>(c->lpart, lblocks, 1.0 / (6.0 * (double)V), c->lsum);
     const dim3 wg(c->nchunk, 27);
@@ -429,12 +486,16 @@ static cudaError_t net_backward(dns_net_ctx *c, const float *tau) {
     k_wgrad<32, OUTP><<<wg, 256, 0, c->stream>>>(c->n, c->dY3, c->A2, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
     k_wgrad_reduce<<<nblk(27 * OUTP * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, OUTP, 32, c->gw3);
     k_colsum<<<OUTP, 256, 0, c->stream>>>(c->dY3, V, OUTP, 6, c->gb + 64);
-    k_conv<OUTP, 32, EPI_DGRAD><<<blocks, 128, 0, c->stream>>>(c->n, c->dY3, c->W3f, nullptr, nullptr, c->dZ2, c->Z2);
+    if ((e = conv<OUTP, 32, EPI_DGRAD>(c->n, c->dY3, c->W3f, nullptr, nullptr, c->dZ2, c->Z2, c->stream)) !=
+        cudaSuccess)
+        return e;
     // layer 2
     k_wgrad<32, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ2, c->A1, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
     k_wgrad_reduce<<<nblk(27 * 32 * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, 32, 32, c->gw2);
     k_colsum<<<32, 256, 0, c->stream>>>(c->dZ2, V, 32, 32, c->gb + 32);
-    k_conv<32, 32, EPI_DGRAD><<<blocks, 128, 0, c->stream>>>(c->n, c->dZ2, c->W2f, nullptr, nullptr, c->dZ1, c->Z1);
+    if ((e = conv<32, 32, EPI_DGRAD>(c->n, c->dZ2, c->W2f, nullptr, nullptr, c->dZ1, c->Z1, c->stream)) !=
+        cudaSuccess)
+        return e;
     // layer 1
     k_wgrad<16, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ1, c->X0, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
     k_wgrad_reduce<<<nblk(27 * 32 * 16), 256, 0, c->stream>>>(c->wpart, c->nchunk, 32, 16, c->gw1);
@@ -520,7 +581,9 @@ int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *o
     if (cudaMemcpy(c->p, h.data(), sizeof(float) * NET_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->m, 0, sizeof(float) * NET_PARAMS) != cudaSuccess ||
         cudaMemset(c->v, 0, sizeof(float) * NET_PARAMS) != cudaSuccess || net_pack(c) != cudaSuccess ||
-        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        conv_attr<16, 32, EPI_HIDDEN>() != cudaSuccess || conv_attr<32, 32, EPI_HIDDEN>() != cudaSuccess ||
+        conv_attr<32, OUTP, EPI_OUT>() != cudaSuccess || conv_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess ||
+        conv_attr<32, 32, EPI_DGRAD>() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
         net_release(c);
         return DNS_ERR_CUDA;
     }

@@ -722,68 +722,113 @@ __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::
 
 // P5b: pointwise over the stored modes: Leray projection (Eq. pressure,
 // NSfinal), viscous term and the RK4 stage (or the bare RHS / transform).
+// Update of one stored mode (ix, iy, kz) of box `box` from its nonlinear
+// term n0..n2: optional forcing, Leray projection (Eq. pressure / NSfinal),
+// viscous term and the RK4 (or IF-RK4) stage, then omega^ of the next stage
+// input for the next P1.
+template <typename real, typename acc>
+__device__ __forceinline__ void p5_mode_update(const Geo &g, const UpdateArgs<real, acc> &args, long long box, int ix,
+                                               int iy, int kz, typename CT<real>::t n0, typename CT<real>::t n1,
+                                               typename CT<real>::t n2) {
+    typedef typename CT<real>::t cplx;
+    typedef typename CT<acc>::t cacc;
+    const long long sS = g.sS;
+    const long long m = box * g.bS + ((long long)ix * g.Kx + iy) * g.Kzp + kz;  // state element, component 0
+    const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
+    if (args.Fext && args.stage != -2) {
+        const cplx f0 = args.Fext[m], f1 = args.Fext[sS + m], f2 = args.Fext[2 * sS + m];
+        n0 = cadd(n0, f0);
+        n1 = cadd(n1, f1);
+        n2 = cadd(n2, f2);
+    }
+    if (args.stage == -2) {  // bare forward transform (physical input)
+        args.dU[m] = cmk<cacc>(n0.x, n0.y);
+        args.dU[sS + m] = cmk<cacc>(n1.x, n1.y);
+        args.dU[2 * sS + m] = cmk<cacc>(n2.x, n2.y);
+        return;
+    }
+    const real kx = (real)compact_to_k(ix, g.K), ky = (real)compact_to_k(iy, g.K), kzr = (real)kz;
+    const real k2 = kx * kx + ky * ky + kzr * kzr;
+    const real inv = k2 > 0 ? (real)1 / k2 : (real)0;
+    const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
+    const real dim = (kx * n0.y + ky * n1.y + kzr * n2.y) * inv;
+    const cplx u0 = args.U[m], u1 = args.U[sS + m], u2 = args.U[2 * sS + m];
+    cplx x0, x1, x2;
+    if (args.ifrk && args.stage >= 0) {
+        // integrating factor: the stage value is the projected nonlinear term
+        // alone; the viscous decay enters through E1 = exp(-nu k^2 dt/2),
+        // E2 = exp(-nu k^2 dt), evaluated in the accumulator precision
+        const acc L = (acc)nu * (acc)k2;
+        const acc e1 = exp(-L * (acc)(0.5 * args.dt)), e2 = exp(-L * (acc)args.dt);
+        x0 = rk_update_if<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre, n0.y - kx * dim), e1, e2);
+        x1 = rk_update_if<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre, n1.y - ky * dim), e1, e2);
+        x2 = rk_update_if<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre, n2.y - kzr * dim), e1, e2);
+    } else {
+        const real vk = nu * k2;
+        x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
+        x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
+        x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+    }
+    if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
+        cplx ox, oy, oz;
+        curl_mode<cplx, real>(kx, ky, kzr, x0, x1, x2, ox, oy, oz);
+        args.Om[m] = ox;
+        args.Om[sS + m] = oy;
+        args.Om[2 * sS + m] = oz;
+    }
+}
+
 template <typename real, typename acc>
 __global__ void k_p5b_update(Geo g, const typename CT<real>::t *__restrict__ Nh, UpdateArgs<real, acc> args) {
     typedef typename CT<real>::t cplx;
-    typedef typename CT<acc>::t cacc;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
+    const int Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
     const long long sS = g.sS;
-    const long long total = sS * g.nb;
     // one mode per thread (no grid-stride loop): every thread's loads are
     // independent, which keeps enough bytes in flight
-    {
-        const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-        if (e >= total) return;
-        const long long box = e / sS, mm = e % sS;
-        const int kz = (int)(mm % Kzp);
-        if (kz >= Kz) return;
-        const long long r = mm / Kzp;
-        const int iy = (int)(r % Kx), ix = (int)(r / Kx);
-        const long long nm = box * g.bB + mm;  // N^ lives in B, state layout
-        const long long m = box * g.bS + mm;   // state element, component 0
-        const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
-        cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
-        if (args.Fext && args.stage != -2) {
-            const cplx f0 = args.Fext[m], f1 = args.Fext[sS + m], f2 = args.Fext[2 * sS + m];
-            n0 = cadd(n0, f0);
-            n1 = cadd(n1, f1);
-            n2 = cadd(n2, f2);
-        }
-        if (args.stage == -2) {  // bare forward transform (physical input)
-            args.dU[m] = cmk<cacc>(n0.x, n0.y);
-            args.dU[sS + m] = cmk<cacc>(n1.x, n1.y);
-            args.dU[2 * sS + m] = cmk<cacc>(n2.x, n2.y);
-            return;
-        }
-        const real kx = (real)compact_to_k(ix, K), ky = (real)compact_to_k(iy, K), kzr = (real)kz;
-        const real k2 = kx * kx + ky * ky + kzr * kzr;
-        const real inv = k2 > 0 ? (real)1 / k2 : (real)0;
-        const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
-        const real dim = (kx * n0.y + ky * n1.y + kzr * n2.y) * inv;
-        const cplx u0 = args.U[m], u1 = args.U[sS + m], u2 = args.U[2 * sS + m];
-        cplx x0, x1, x2;
-        if (args.ifrk && args.stage >= 0) {
-            // integrating factor: the stage value is the projected nonlinear term
-            // alone; the viscous decay enters through E1 = exp(-nu k^2 dt/2),
-            // E2 = exp(-nu k^2 dt), evaluated in the accumulator precision
-            const acc L = (acc)nu * (acc)k2;
-            const acc e1 = exp(-L * (acc)(0.5 * args.dt)), e2 = exp(-L * (acc)args.dt);
-            x0 = rk_update_if<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre, n0.y - kx * dim), e1, e2);
-            x1 = rk_update_if<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre, n1.y - ky * dim), e1, e2);
-            x2 = rk_update_if<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre, n2.y - kzr * dim), e1, e2);
-        } else {
-            const real vk = nu * k2;
-            x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
-            x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
-            x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
-        }
-        if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
-            cplx ox, oy, oz;
-            curl_mode<cplx, real>(kx, ky, kzr, x0, x1, x2, ox, oy, oz);
-            args.Om[m] = ox;
-            args.Om[sS + m] = oy;
-            args.Om[2 * sS + m] = oz;
-        }
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= sS * g.nb) return;
+    const long long box = e / sS, mm = e % sS;
+    const int kz = (int)(mm % Kzp);
+    if (kz >= Kz) return;
+    const long long r = mm / Kzp;
+    const int iy = (int)(r % Kx), ix = (int)(r / Kx);
+    const long long nm = box * g.bB + mm;  // N^ lives in B, state layout
+    const cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
+    p5_mode_update<real, acc>(g, args, box, ix, iy, kz, n0, n1, n2);
+}
+
+// P5a and P5b in one pass: a block transforms all three fields of one
+// (ky, kz tile) along x (tile columns f*W + c), keeps the result in shared
+// memory, and updates the Kx x W stored modes of the tile from it, so the
+// nonlinear term never goes to HBM.
+template <typename real, typename acc, int N, int W, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                const typename CT<real>::t *__restrict__ A,
+                                                UpdateArgs<real, acc> args) {
+    typedef typename CT<real>::t cplx;
+    constexpr int WT = 3 * W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
+    cplx *tile = tw + N;
+    load_twiddles<real>(tw, twg, N);
+    __syncthreads();
+    const int box = blockIdx.x, kz0 = blockIdx.y * W, jy = blockIdx.z;
+    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
+    const cplx *src = A + box * g.bA + (long long)jy * Kzp + kz0;
+    auto load = [&](int n, int c) -> cplx {
+        const int f = c / W, cc = c % W;
+        if (kz0 + cc >= Kz) return cmk<cplx>(0.0, 0.0);
+        return src[f * g.sA + (long long)n * Kx * Kzp + cc];
+    };
+    auto tstore = [&](int n, int c, cplx v) { tile[n * WT + c] = v; };
+    TileFFT<real, N, WT, T, -1, MAXR>::run(tile, WT, tw, load, tstore);
+    for (int e = threadIdx.x; e < Kx * W; e += T) {
+        const int ix = e / W, cc = e % W, kz = kz0 + cc;
+        if (kz >= Kz) continue;
+        const int kx = compact_to_k(ix, K);
+        const int n = kx >= 0 ? kx : kx + N;
+        const cplx *row = tile + n * WT + cc;
+        p5_mode_update<real, acc>(g, args, box, ix, jy, kz, row[0], row[W], row[2 * W]);
     }
 }
 

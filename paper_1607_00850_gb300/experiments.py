@@ -249,6 +249,73 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
     return report
 
 
+def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> dict:
+    """Cost of the learned closure on the GPU: the network forward on one n^3
+    sample (flops = 2 n^3 27 (9*32 + 32*32 + 32*6), the contraction the
+    tensor cores run; the input channels are padded to 16 and the output to
+    16 on the device, which is not counted), one Adam training step per
+    sample, and one LES step at n^3 without a model, with Smagorinsky and
+    with the learned closure, next to one DNS step at dns_N^3.  Times by CUDA
+    events on the default stream (forward) and wall clock around
+    synchronised step loops."""
+    import torch
+    dev = torch.device("cuda")
+    flops = 2.0 * n ** 3 * 27 * (9 * 32 + 32 * 32 + 32 * 6)
+    net = dns.dns_net_create(n, seed=1)
+    out = {"n": n, "forward_flops": flops}
+    try:
+        gen = torch.Generator(device=dev).manual_seed(7)
+        g = torch.randn((9, n, n, n), device=dev, generator=gen)
+        tau = torch.empty((6, n, n, n), device=dev)
+        G = torch.randn((batch, 9, n, n, n), device=dev, generator=gen)
+        T = torch.randn((batch, 6, n, n, n), device=dev, generator=gen)
+        for _ in range(3):
+            dns.dns_net_forward(net, g, tau)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            dns.dns_net_forward(net, g, tau)
+        b.record()
+        b.synchronize()
+        fwd = a.elapsed_time(b) / reps
+        out["forward_ms"] = fwd
+        out["forward_tflops"] = flops / (fwd / 1e3) / 1e12
+        dns.dns_net_train_step(net, batch, G, T, 1e-4)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = max(1, reps // 4)
+        for _ in range(k):
+            dns.dns_net_train_step(net, batch, G, T, 1e-4)
+        torch.cuda.synchronize()
+        out["train_ms_per_sample"] = (time.perf_counter() - t0) / (k * batch) * 1e3
+        with dns.Solver(n, 1e-3, 2e-3, dns.DNS_F32) as s:
+            s.set_velocity(inputs.random_isotropic(n, seed=3))
+            for mode in ("no_model", "smagorinsky", "learned"):
+                if mode == "learned":
+                    dns.dns_les_set_closure(s.h, net)
+                elif mode == "smagorinsky":
+                    dns.dns_les_set_smagorinsky(s.h, 0.17)
+                s.step(3)
+                s.synchronize()
+                t0 = time.perf_counter()
+                s.step(reps)
+                s.synchronize()
+                out[f"les_step_ms_{mode}"] = (time.perf_counter() - t0) / reps * 1e3
+                dns.dns_les_set_closure(s.h, None)
+        with dns.Solver(dns_N, 1e-3, 2e-3, dns.DNS_F32) as s:
+            s.set_velocity(inputs.random_isotropic(dns_N, seed=3))
+            s.step(3)
+            s.synchronize()
+            t0 = time.perf_counter()
+            s.step(reps)
+            s.synchronize()
+            out[f"dns_step_ms_{dns_N}"] = (time.perf_counter() - t0) / reps * 1e3
+    finally:
+        dns.dns_net_free(net)
+    return out
+
+
 def main(argv=None):
     p = argparse.ArgumentParser()
     sub = p.add_subparsers(dest="cmd", required=True)
@@ -258,6 +325,8 @@ def main(argv=None):
     q.add_argument("--dt", type=float, default=1e-3)
     q.add_argument("--every", type=int, default=1000)
     q.add_argument("--ifrk4", action="store_true")
+    q = sub.add_parser("les-bench")
+    q.add_argument("--n", type=int, default=64)
     q = sub.add_parser("les")
     q.add_argument("--N", type=int, default=256)
     q.add_argument("--n", type=int, default=64)
@@ -271,6 +340,10 @@ def main(argv=None):
     q.add_argument("--eval-steps", type=int, default=500)
     q.add_argument("--out", default=None, help="write the full report (JSON) here")
     args = p.parse_args(argv)
+    if args.cmd == "les-bench":
+        dns.load()
+        print(json.dumps(les_bench(args.n)), flush=True)
+        return
     if args.cmd == "les":
         dns.load()
         rep = les_closure(args.N, args.n, seeds=args.seeds, snaps=args.snaps, spinup=args.spinup,
