@@ -288,9 +288,44 @@ struct TileFFT {
 __host__ __device__ constexpr int row_ld(int N) { return N + N / 16; }
 __device__ __forceinline__ int radd(int n) { return n + (n >> 4); }
 
+// Per-stage twiddle tables for the row engine.  In stage s >= 1 work item j
+// multiplies input r by w^(r k TWS), k = j mod Ns; neighbouring items read
+// entries r k TWS apart in the N-entry table, which puts many lanes of a warp
+// on one shared-memory bank for the larger r.  The table of stage s instead
+// stores those factors as [k][r - 1] (Ns (R - 1) entries), so lanes read
+// R - 1 entries apart: an odd stride, free of bank conflicts.  The tables of
+// all stages follow each other; twt_size rounds their total up to even so
+// what follows stays 16-byte aligned.
+__host__ __device__ constexpr int twt_offset(int N, int MAXR, int S) {
+    FftPlan p = make_plan(N, MAXR);
+    int off = 0;
+    for (int s = 1; s < S && s < p.nst; ++s) off += p.ns[s] * (p.r[s] - 1);
+    return off;
+}
+__host__ __device__ constexpr int twt_size(int N, int MAXR) {
+    const int t = twt_offset(N, MAXR, 64);
+    return (t + 1) / 2 * 2;
+}
+// Fill the stage tables (twt_size entries at twt) from the N-entry table in
+// global memory; every thread of the block takes part.
+template <typename cplx, int N, int MAXR, int S = 1>
+__device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg) {
+    constexpr FftPlan P = make_plan(N, MAXR);
+    if constexpr (S < P.nst) {
+        constexpr int R = P.r[S], Ns = P.ns[S], TWS = N / (Ns * R), off = twt_offset(N, MAXR, S);
+        for (int e = threadIdx.x; e < Ns * (R - 1); e += blockDim.x) {
+            const int k = e / (R - 1), r = e % (R - 1) + 1;
+            twt[off + e] = twg[r * k * TWS];
+        }
+        build_twt<cplx, N, MAXR, S + 1>(twt, twg);
+    }
+}
+
 // ONE = true runs stage S alone (its output stays in the tile unless S is
 // the last stage), so a caller can act between the first stage and the rest.
-template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0, bool ONE = false>
+// TWT = true reads the twiddles of stages >= 1 from the per-stage tables at
+// tw + N (see build_twt) instead of the N-entry table.
+template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0, bool ONE = false, bool TWT = false>
 struct RowFFT {
     typedef typename CT<real>::t cplx;
     // Load(v, n): first-stage input; Store(v, n, x): last-stage output.
@@ -320,9 +355,10 @@ struct RowFFT {
                 }
                 if constexpr (!first) {
                     const int k = j % Ns;
+                    const cplx *tk = tw + N + twt_offset(N, MAXR, S) + k * (R - 1) - 1;
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
-                        cplx w = tw[r * k * TWS];
+                        cplx w = TWT ? tk[r] : tw[r * k * TWS];
                         if (SIGN > 0) w.y = -w.y;
                         v[q][r] = cmul(v[q][r], w);
                     }
@@ -346,7 +382,7 @@ struct RowFFT {
             }
         }
         __syncthreads();
-        if constexpr (!last && !ONE) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1>::run(tile, tw, load, store);
+        if constexpr (!last && !ONE) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1, false, TWT>::run(tile, tw, load, store);
     }
 };
 

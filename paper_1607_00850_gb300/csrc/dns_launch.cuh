@@ -81,8 +81,8 @@ template <typename real, int N, int V> struct P3Shape {
     typedef typename CT<real>::t cplx;
     static constexpr bool ASYNC = VT::p3A[V] == 1;
     static constexpr bool BULK = VT::p3A[V] == 2;
-    static constexpr size_t smem =
-        ASYNC ? P3Stage<real, N, L>::smem : sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
+    static constexpr size_t smem = ASYNC ? P3Stage<real, N, L, R3>::smem
+                                         : sizeof(cplx) * (size_t)(N + twt_size(N, R3) + 3 * L * row_ld(N));
     static constexpr int MINB = VT::p3M[V];
     static constexpr bool valid = (V == 0 || (N >= 64 && (lmax >> VT::p3S[V]) >= 1)) && T <= 1024 &&
                                   smem <= kMaxSmem && (MINB == 1 || (2 * smem <= kMaxSmem && 2 * T <= 1024));

@@ -289,7 +289,7 @@ __device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>
             }
         }
         __syncthreads();
-        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1>::run(tile, tw, noload, tstore);
+        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1, false, true>::run(tile, tw, noload, tstore);
     }
     for (int e = threadIdx.x; e < L * (K + 1); e += T) {
         const int kz = e % (K + 1), l = e / (K + 1);
@@ -322,9 +322,10 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
     typedef typename CT<real>::t cplx;
     constexpr int LDR = row_ld(N);
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
-    cplx *tile = tw + N;  // [3L][LDR]: pair p of line l at row p*L + l
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);  // N twiddles, then the per-stage tables
+    cplx *tile = tw + N + twt_size(N, MAXR);         // [3L][LDR]: pair p of line l at row p*L + l
     load_twiddles<real>(tw, twg, N);
+    build_twt<cplx, N, MAXR>(tw + N, twg);
     __syncthreads();
     const int K = g.K, Kzp = g.Kzp;
     const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
@@ -340,7 +341,7 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
         return p3_pack(B[(2 * p) * sB + off], B[(2 * p + 1) * sB + off], n, kz, N);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
-    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
+    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
     p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B, line0);
 }
 
@@ -363,13 +364,14 @@ __global__ void __launch_bounds__(T, 2) k_p3_z_cross_2b(Geo g, const typename CT
 // copied into a shared staging buffer, and the copy of the next group is
 // issued as soon as the first inverse stage has consumed the current one, so
 // it overlaps the rest of the group's transforms.  Shared memory:
-// twiddles [N] | tile [3L][row_ld(N)] | staging [6][L][Kzp] (16-byte aligned).
+// twiddles [N] and per-stage tables | tile [3L][row_ld(N)] | staging
+// [6][L][Kzp] (16-byte aligned).
 // A copy that does not complete within the wait limit sets g.err and ends
 // the block.
-template <typename real, int N, int L> struct P3Stage {
+template <typename real, int N, int L, int MAXR = 8> struct P3Stage {
     typedef typename CT<real>::t cplx;
     static constexpr int KZP = ((N - 1) / 3 + 1 + 3) / 4 * 4;
-    static constexpr size_t head = sizeof(cplx) * (size_t)(N + 3 * L * row_ld(N));
+    static constexpr size_t head = sizeof(cplx) * (size_t)(N + twt_size(N, MAXR) + 3 * L * row_ld(N));
     static constexpr size_t off = (head + 15) / 16 * 16;
     static constexpr size_t field_bytes = sizeof(cplx) * (size_t)L * KZP;
     static constexpr size_t smem = off + 6 * field_bytes;
@@ -411,14 +413,14 @@ __device__ __noinline__ void p3_tma_group(Geo g, const typename CT<real>::t *tw,
         return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
-    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, true>::run(tile, tw, iload, tstore);
+    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, true, true>::run(tile, tw, iload, tstore);
     // the staging buffer is free: fetch the next group while this one finishes
     if (threadIdx.x == 0 && next >= 0) {
         fence_proxy_async_smem();
         p3_issue<real, N, L>(g, B, stage, bar, next);
     }
     constexpr FftPlan P = make_plan(N, MAXR);
-    if constexpr (P.nst > 1) RowFFT<real, N, 3 * L, T, +1, MAXR, 1>::run(tile, tw, iload, tstore);
+    if constexpr (P.nst > 1) RowFFT<real, N, 3 * L, T, +1, MAXR, 1, false, true>::run(tile, tw, iload, tstore);
     p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
 }
 
@@ -426,14 +428,15 @@ template <typename real, int N, int L, int T, int MAXR>
 __device__ __forceinline__ void p3_tma_body(Geo g, const typename CT<real>::t *__restrict__ twg,
                                             typename CT<real>::t *__restrict__ B, long long ngroups) {
     typedef typename CT<real>::t cplx;
-    typedef P3Stage<real, N, L> PS;
+    typedef P3Stage<real, N, L, MAXR> PS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
-    cplx *tile = tw + N;
+    cplx *tile = tw + N + twt_size(N, MAXR);
     cplx *stage = reinterpret_cast<cplx *>(smem_raw + PS::off);
     load_twiddles<real>(tw, twg, N);
+    build_twt<cplx, N, MAXR>(tw + N, twg);
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     long long grp = blockIdx.x;
@@ -472,14 +475,15 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
     __shared__ __align__(8) uint64_t bar;
     __shared__ int s_ok;
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
-    cplx *tile = tw + N;
-    cplx *stage = tile;  // 16-byte aligned: N complex values precede it
+    cplx *tile = tw + N + twt_size(N, MAXR);
+    cplx *stage = tile;  // 16-byte aligned: an even number of complex values precede it
     const long long grp = blockIdx.x;
     if (threadIdx.x == 0) {
         mbar_init(&bar, 1);
         p3_issue<real, N, L>(g, B, stage, &bar, grp);
     }
     load_twiddles<real>(tw, twg, N);
+    build_twt<cplx, N, MAXR>(tw + N, twg);
     if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
     __syncthreads();
     if (!s_ok) {
@@ -501,7 +505,7 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
         return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
-    RowFFT<real, N, 3 * L, T, +1, MAXR>::run(tile, tw, iload, tstore);
+    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
     p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
 }
 
