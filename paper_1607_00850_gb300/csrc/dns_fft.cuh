@@ -84,6 +84,23 @@ __host__ __device__ constexpr FftPlan make_plan(int N, int MAXR = 8) {
     return p;
 }
 
+// The same radices in the opposite order (larger first): an inverse run
+// with this plan ends with the radix a forward run with make_plan starts
+// with, so its last stage leaves each work item exactly the points the
+// forward first stage needs (positions j + r N / R).
+__host__ __device__ constexpr FftPlan make_plan_rev(int N, int MAXR = 8) {
+    FftPlan f = make_plan(N, MAXR);
+    FftPlan p{f.nst, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
+    for (int s = 0; s < f.nst; ++s) p.r[s] = f.r[f.nst - 1 - s];
+    int ns = 1;
+    for (int s = 0; s < p.nst; ++s) { p.ns[s] = ns; ns *= p.r[s]; }
+    return p;
+}
+
+__host__ __device__ constexpr FftPlan plan_of(int N, int MAXR, bool rev) {
+    return rev ? make_plan_rev(N, MAXR) : make_plan(N, MAXR);
+}
+
 __host__ __device__ constexpr int plan_max_radix(int N, int MAXR = 8) {
     FftPlan p = make_plan(N, MAXR);
     int m = 1;
@@ -296,42 +313,47 @@ __device__ __forceinline__ int radd(int n) { return n + (n >> 4); }
 // R - 1 entries apart: an odd stride, free of bank conflicts.  The tables of
 // all stages follow each other; twt_size rounds their total up to even so
 // what follows stays 16-byte aligned.
-__host__ __device__ constexpr int twt_offset(int N, int MAXR, int S) {
-    FftPlan p = make_plan(N, MAXR);
+__host__ __device__ constexpr int twt_offset(int N, int MAXR, int S, bool rev = false) {
+    FftPlan p = plan_of(N, MAXR, rev);
     int off = 0;
     for (int s = 1; s < S && s < p.nst; ++s) off += p.ns[s] * (p.r[s] - 1);
     return off;
 }
-__host__ __device__ constexpr int twt_size(int N, int MAXR) {
-    const int t = twt_offset(N, MAXR, 64);
+__host__ __device__ constexpr int twt_size(int N, int MAXR, bool rev = false) {
+    const int t = twt_offset(N, MAXR, 64, rev);
     return (t + 1) / 2 * 2;
 }
-// Fill the stage tables (twt_size entries at twt) from the N-entry table in
-// global memory; every thread of the block takes part.
-template <typename cplx, int N, int MAXR, int S = 1>
+// Fill the stage tables of one plan (twt_size entries at twt) from the
+// N-entry table in global memory; every thread of the block takes part.
+// Kernels that also run the reversed plan keep its tables right after the
+// forward plan's: tw [N] | forward tables | reversed tables.
+template <typename cplx, int N, int MAXR, bool REV = false, int S = 1>
 __device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg) {
-    constexpr FftPlan P = make_plan(N, MAXR);
+    constexpr FftPlan P = plan_of(N, MAXR, REV);
     if constexpr (S < P.nst) {
-        constexpr int R = P.r[S], Ns = P.ns[S], TWS = N / (Ns * R), off = twt_offset(N, MAXR, S);
+        constexpr int R = P.r[S], Ns = P.ns[S], TWS = N / (Ns * R), off = twt_offset(N, MAXR, S, REV);
         for (int e = threadIdx.x; e < Ns * (R - 1); e += blockDim.x) {
             const int k = e / (R - 1), r = e % (R - 1) + 1;
             twt[off + e] = twg[r * k * TWS];
         }
-        build_twt<cplx, N, MAXR, S + 1>(twt, twg);
+        build_twt<cplx, N, MAXR, REV, S + 1>(twt, twg);
     }
 }
 
 // ONE = true runs stage S alone (its output stays in the tile unless S is
 // the last stage), so a caller can act between the first stage and the rest.
 // TWT = true reads the twiddles of stages >= 1 from the per-stage tables at
-// tw + N (see build_twt) instead of the N-entry table.
-template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0, bool ONE = false, bool TWT = false>
+// tw + N (see build_twt) instead of the N-entry table.  REVP runs the
+// reversed plan (make_plan_rev); SKIPLAST stops before the plan's last
+// stage, leaving its input in the tile.
+template <typename real, int N, int NV, int T, int SIGN, int MAXR, int S = 0, bool ONE = false, bool TWT = false,
+          bool REVP = false, bool SKIPLAST = false>
 struct RowFFT {
     typedef typename CT<real>::t cplx;
     // Load(v, n): first-stage input; Store(v, n, x): last-stage output.
     template <class Load, class Store>
     static __device__ __forceinline__ void run(cplx *tile, const cplx *tw, const Load &load, const Store &store) {
-        constexpr FftPlan P = make_plan(N, MAXR);
+        constexpr FftPlan P = plan_of(N, MAXR, REVP);
         constexpr int R = P.r[S];
         constexpr int Ns = P.ns[S];
         constexpr int NB = N / R;
@@ -355,7 +377,8 @@ struct RowFFT {
                 }
                 if constexpr (!first) {
                     const int k = j % Ns;
-                    const cplx *tk = tw + N + twt_offset(N, MAXR, S) + k * (R - 1) - 1;
+                    const cplx *tk = tw + N + (REVP ? twt_size(N, MAXR) : 0) + twt_offset(N, MAXR, S, REVP) +
+                                     k * (R - 1) - 1;
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
                         cplx w = TWT ? tk[r] : tw[r * k * TWS];
@@ -382,7 +405,8 @@ struct RowFFT {
             }
         }
         __syncthreads();
-        if constexpr (!last && !ONE) RowFFT<real, N, NV, T, SIGN, MAXR, S + 1, false, TWT>::run(tile, tw, load, store);
+        if constexpr (!last && !ONE && !(SKIPLAST && S + 2 == P.nst))
+            RowFFT<real, N, NV, T, SIGN, MAXR, S + 1, false, TWT, REVP, SKIPLAST>::run(tile, tw, load, store);
     }
 };
 

@@ -22,26 +22,27 @@ constexpr size_t kMaxSmem = 227 * 1024;
 template <typename real> struct VariantTable;
 // P3 variants: lines per block lmax >> p3S (lmax = the most lines that fit
 // 512 threads), radix cap p3R, blocks the compiler keeps resident p3M, and
-// how the input arrives, p3A: 0 loads by the threads, 1 persistent blocks
-// fed by bulk asynchronous copies (next group prefetched), 2 one group per
-// block by one bulk copy into the tile.
+// how the input arrives and is processed, p3A: 0 loads by the threads, 1
+// persistent blocks fed by bulk asynchronous copies (next group
+// prefetched), 2 one group per block by one bulk copy into the tile, 3 as 2
+// with the inverse-last / cross / forward-first stages fused in registers.
 template <> struct VariantTable<float> {
     static constexpr int BUD = 32;
     static constexpr int colW[3] = {16, 32, 16};
     static constexpr int colR[3] = {16, 16, 8};
-    static constexpr int p3S[11] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1};
-    static constexpr int p3R[11] = {32, 32, 32, 32, 32, 16, 32, 32, 32, 32, 32};
-    static constexpr int p3M[11] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2};
-    static constexpr int p3A[11] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2};
+    static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
+    static constexpr int p3R[14] = {32, 32, 32, 32, 32, 16, 32, 32, 32, 32, 32, 32, 32, 32};
+    static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
+    static constexpr int p3A[14] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2, 3, 3, 3};
 };
 template <> struct VariantTable<double> {
     static constexpr int BUD = 16;
     static constexpr int colW[3] = {8, 16, 8};
     static constexpr int colR[3] = {8, 8, 16};
-    static constexpr int p3S[11] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1};
-    static constexpr int p3R[11] = {16, 16, 16, 16, 16, 8, 16, 16, 16, 16, 16};
-    static constexpr int p3M[11] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2};
-    static constexpr int p3A[11] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2};
+    static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
+    static constexpr int p3R[14] = {16, 16, 16, 16, 16, 8, 16, 16, 16, 16, 16, 16, 16, 16};
+    static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
+    static constexpr int p3A[14] = {0, 0, 0, 0, 0, 0, 1, 1, 2, 2, 2, 3, 3, 3};
 };
 
 __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
@@ -81,8 +82,10 @@ template <typename real, int N, int V> struct P3Shape {
     typedef typename CT<real>::t cplx;
     static constexpr bool ASYNC = VT::p3A[V] == 1;
     static constexpr bool BULK = VT::p3A[V] == 2;
-    static constexpr size_t smem = ASYNC ? P3Stage<real, N, L, R3>::smem
-                                         : sizeof(cplx) * (size_t)(N + twt_size(N, R3) + 3 * L * row_ld(N));
+    static constexpr bool BULKF = VT::p3A[V] == 3;
+    static constexpr size_t smem =
+        ASYNC ? P3Stage<real, N, L, R3>::smem
+              : sizeof(cplx) * (size_t)(N + twt_size(N, R3) + (BULKF ? twt_size(N, R3, true) : 0) + 3 * L * row_ld(N));
     static constexpr int MINB = VT::p3M[V];
     static constexpr bool valid = (V == 0 || (N >= 64 && (lmax >> VT::p3S[V]) >= 1)) && T <= 1024 &&
                                   smem <= kMaxSmem && (MINB == 1 || (2 * smem <= kMaxSmem && 2 * T <= 1024));
@@ -153,6 +156,16 @@ template <typename real, int N, int V> struct P3Launch {
         if constexpr (S::MINB == 2) return k_p3_z_tma_2b<real, N, S::L, S::T, S::R3>;
         else return k_p3_z_tma<real, N, S::L, S::T, S::R3>;
     }
+    typedef void (*BulkKernel)(Geo, const cplx *, cplx *);
+    static BulkKernel bulk_kernel() {
+        if constexpr (S::BULKF) {
+            if constexpr (S::MINB == 2) return k_p3_z_bulkf_2b<real, N, S::L, S::T, S::R3>;
+            else return k_p3_z_bulkf<real, N, S::L, S::T, S::R3>;
+        } else {
+            if constexpr (S::MINB == 2) return k_p3_z_bulk_2b<real, N, S::L, S::T, S::R3>;
+            else return k_p3_z_bulk<real, N, S::L, S::T, S::R3>;
+        }
+    }
     static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
         if constexpr (S::ASYNC) {
             // bulk copies need 16-byte aligned rows of the stated padding
@@ -161,15 +174,10 @@ template <typename real, int N, int V> struct P3Launch {
             const long long groups = (long long)N * N / S::L * g.nb;
             const unsigned grid = (unsigned)(groups < resident ? groups : resident);
             tma_kernel()<<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B, groups);
-        } else if constexpr (S::BULK) {
+        } else if constexpr (S::BULK || S::BULKF) {
             if (g.Kzp != P3Stage<real, N, S::L>::KZP || ((uintptr_t)B & 15)) return cudaErrorInvalidValue;
             dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
-            if constexpr (S::MINB == 2)
-                k_p3_z_bulk_2b<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
-                                                                                      (cplx *)B);
-            else
-                k_p3_z_bulk<real, N, S::L, S::T, S::R3><<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw,
-                                                                                   (cplx *)B);
+            bulk_kernel()<<<grid, S::T, S::smem, st>>>(g, (const cplx *)tw, (cplx *)B);
         } else {
             dim3 grid((unsigned)((long long)N * N / S::L * g.nb));
             if constexpr (S::MINB == 2)
@@ -190,9 +198,8 @@ template <typename real, int N, int V> struct P3Launch {
             if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, tma_kernel(), S::T, S::smem);
             if (e == cudaSuccess) resident = sms * (occ > 0 ? occ : 1);
             return e;
-        } else if constexpr (S::BULK) {
-            if constexpr (S::MINB == 2) return set_smem(k_p3_z_bulk_2b<real, N, S::L, S::T, S::R3>, S::smem);
-            else return set_smem(k_p3_z_bulk<real, N, S::L, S::T, S::R3>, S::smem);
+        } else if constexpr (S::BULK || S::BULKF) {
+            return set_smem(bulk_kernel(), S::smem);
         } else if constexpr (S::MINB == 2) {
             return set_smem(k_p3_z_cross_2b<real, N, S::L, S::T, S::R3>, S::smem);
         } else {

@@ -240,16 +240,107 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
 // c2 = a0 b1 - a1 b0; line l becomes Nx + i Ny, line L + l becomes Nz + 0i),
 // the remaining stages, then the two real transforms of line l unpacked and
 // kz <= K stored to fields 0..2 of B (already offset to the box).
+// Forward stages >= 1 of the 2L packed lines (stage 0 output in the tile),
+// then the two real transforms of line l unpacked and kz <= K stored to
+// fields 0..2 of B (already offset to the box).
 template <typename real, int N, int L, int T, int MAXR>
-__device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>::t *tile,
-                                                 const typename CT<real>::t *tw, typename CT<real>::t *B,
-                                                 long long line0) {
+__device__ __forceinline__ void p3_fwd_rest_store(const Geo &g, typename CT<real>::t *tile,
+                                                  const typename CT<real>::t *tw, typename CT<real>::t *B,
+                                                  long long line0) {
     typedef typename CT<real>::t cplx;
     constexpr int LDR = row_ld(N);
     const int K = g.K, Kzp = g.Kzp;
     const long long sB = g.sB;
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     auto noload = [&](int, int) -> cplx { return cmk<cplx>(0.0, 0.0); };
+    constexpr FftPlan P = make_plan(N, MAXR);
+    if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1, false, true>::run(tile, tw, noload, tstore);
+    for (int e = threadIdx.x; e < L * (K + 1); e += T) {
+        const int kz = e % (K + 1), l = e / (K + 1);
+        const cplx za = tile[l * LDR + radd(kz)];
+        const cplx zm = tile[l * LDR + radd((N - kz) % N)];
+        const cplx zb = tile[(L + l) * LDR + radd(kz)];
+        const long long off = (line0 + l) * Kzp + kz;
+        // X = (Z[k] + conj Z[N-k]) / 2,  Y = (Z[k] - conj Z[N-k]) / (2i)
+        B[off] = cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y));
+        B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
+        B[2 * sB + off] = zb;
+    }
+}
+
+// The middle of P3 in registers: the last stage of the inverse (run with
+// the reversed plan, so its radix R is the forward plan's first) leaves work
+// item (l, j) the physical values of all three packed lines of line l at
+// z = j + r N/R; u x omega of those points feeds the first forward stage
+// directly, whose input positions are the same.  Saves the tile round trip
+// between the two transforms.  Stage-0 forward output goes to the tile.
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_mid_fused(typename CT<real>::t *tile, const typename CT<real>::t *tw) {
+    typedef typename CT<real>::t cplx;
+    constexpr int LDR = row_ld(N);
+    constexpr FftPlan PI = make_plan_rev(N, MAXR), PF = make_plan(N, MAXR);
+    constexpr int SL = PI.nst - 1;
+    constexpr int R = PI.r[SL];
+    static_assert(PI.nst >= 2 && R == PF.r[0], "inverse last radix must equal forward first radix");
+    constexpr int NB = N / R;  // items per line; = PI.ns[SL], the last stage's twiddle period
+    constexpr int TOT = NB * L;
+    constexpr int Q = (TOT + T - 1) / T;
+    const cplx *twl = tw + N + twt_size(N, MAXR) + twt_offset(N, MAXR, SL, true);
+    cplx va[Q][R], vb[Q][R];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int idx = (int)threadIdx.x + q * T;
+        if (Q * T == TOT || idx < TOT) {
+            const int l = idx / NB, j = idx % NB;
+            cplx x2[R];
+#pragma unroll
+            for (int p = 0; p < 3; ++p) {
+                cplx *xp = p == 0 ? va[q] : (p == 1 ? vb[q] : x2);
+#pragma unroll
+                for (int r = 0; r < R; ++r) xp[r] = tile[(p * L + l) * LDR + radd(j + r * NB)];
+#pragma unroll
+                for (int r = 1; r < R; ++r) {
+                    cplx w = twl[j * (R - 1) + r - 1];
+                    w.y = -w.y;  // inverse transform: conjugate twiddles
+                    xp[r] = cmul(xp[r], w);
+                }
+                dft<R, +1>(xp);
+            }
+            // point z = j + r NB: (ux, uy), (uz, wx), (wy, wz) -> Nx + i Ny, Nz + 0i
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const real ux = va[q][r].x, uy = va[q][r].y, uz = vb[q][r].x, wx = vb[q][r].y, wy = x2[r].x,
+                           wz = x2[r].y;
+                va[q][r] = cmk<cplx>(uy * wz - uz * wy, uz * wx - ux * wz);
+                vb[q][r] = cmk<cplx>(ux * wy - uy * wx, 0.0);
+            }
+            dft<R, -1>(va[q]);
+            dft<R, -1>(vb[q]);
+        }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+        const int idx = (int)threadIdx.x + q * T;
+        if (Q * T == TOT || idx < TOT) {
+            const int l = idx / NB, j = idx % NB;
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                const int a = radd(j * R + r);
+                tile[l * LDR + a] = va[q][r];
+                tile[(L + l) * LDR + a] = vb[q][r];
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>::t *tile,
+                                                 const typename CT<real>::t *tw, typename CT<real>::t *B,
+                                                 long long line0) {
+    typedef typename CT<real>::t cplx;
+    constexpr int LDR = row_ld(N);
     {
         constexpr FftPlan P = make_plan(N, MAXR);
         constexpr int R = P.r[0];
@@ -289,19 +380,8 @@ __device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>
             }
         }
         __syncthreads();
-        if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1, false, true>::run(tile, tw, noload, tstore);
     }
-    for (int e = threadIdx.x; e < L * (K + 1); e += T) {
-        const int kz = e % (K + 1), l = e / (K + 1);
-        const cplx za = tile[l * LDR + radd(kz)];
-        const cplx zm = tile[l * LDR + radd((N - kz) % N)];
-        const cplx zb = tile[(L + l) * LDR + radd(kz)];
-        const long long off = (line0 + l) * Kzp + kz;
-        // X = (Z[k] + conj Z[N-k]) / 2,  Y = (Z[k] - conj Z[N-k]) / (2i)
-        B[off] = cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y));
-        B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
-        B[2 * sB + off] = zb;
-    }
+    p3_fwd_rest_store<real, N, L, T, MAXR>(g, tile, tw, B, line0);
 }
 
 // First-stage input of the packed inverse: virtual line vl = p L + l holds
@@ -507,6 +587,67 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
     p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+}
+
+// Bulk-fed P3 with the register-fused middle (p3_mid_fused): shared memory
+// twiddles [N] | forward tables | reversed-plan tables | tile (the staging
+// buffer is the tile's start).
+template <typename real, int N, int L, int T, int MAXR>
+__device__ __forceinline__ void p3_bulkf_body(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                              typename CT<real>::t *__restrict__ B) {
+    typedef typename CT<real>::t cplx;
+    typedef P3Stage<real, N, L> PS;
+    constexpr int LDR = row_ld(N);
+    constexpr int TWTS = twt_size(N, MAXR) + twt_size(N, MAXR, true);
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_ok;
+    cplx *tw = reinterpret_cast<cplx *>(smem_raw);
+    cplx *tile = tw + N + TWTS;
+    cplx *stage = tile;  // 16-byte aligned: an even number of complex values precede it
+    const long long grp = blockIdx.x;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        p3_issue<real, N, L>(g, B, stage, &bar, grp);
+    }
+    load_twiddles<real>(tw, twg, N);
+    build_twt<cplx, N, MAXR>(tw + N, twg);
+    build_twt<cplx, N, MAXR, true>(tw + N + twt_size(N, MAXR), twg);
+    if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
+    __syncthreads();
+    if (!s_ok) {
+        if (threadIdx.x == 0) {
+            record_error(g.err, kErrWaitTimeout);
+            mbar_wait_bounded(&bar, 0);  // let the copy in flight land before the block ends
+        }
+        return;
+    }
+    mbar_try_wait(&bar, 0);  // completed: acquire the copied data in every thread
+    const int K = g.K;
+    const long long NN = (long long)N * N, lineg = grp * L;
+    const long long box = lineg / NN, line0 = lineg % NN;
+    auto iload = [&](int vl, int n) -> cplx {
+        const int p = vl / L, l = vl % L;
+        const int kz = n <= N / 2 ? n : N - n;
+        if (kz > K) return cmk<cplx>(0.0, 0.0);
+        const cplx *row = stage + l * PS::KZP + kz;
+        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+    };
+    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true, true, true>::run(tile, tw, iload, tstore);
+    p3_mid_fused<real, N, L, T, MAXR>(tile, tw);
+    p3_fwd_rest_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+}
+
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T) k_p3_z_bulkf(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                  typename CT<real>::t *__restrict__ B) {
+    p3_bulkf_body<real, N, L, T, MAXR>(g, twg, B);
+}
+template <typename real, int N, int L, int T, int MAXR>
+__global__ void __launch_bounds__(T, 2) k_p3_z_bulkf_2b(Geo g, const typename CT<real>::t *__restrict__ twg,
+                                                        typename CT<real>::t *__restrict__ B) {
+    p3_bulkf_body<real, N, L, T, MAXR>(g, twg, B);
 }
 
 template <typename real, int N, int L, int T, int MAXR>
