@@ -28,8 +28,8 @@ template <typename real> struct VariantTable;
 // with the inverse-last / cross / forward-first stages fused in registers.
 template <> struct VariantTable<float> {
     static constexpr int BUD = 32;
-    static constexpr int colW[3] = {16, 32, 16};
-    static constexpr int colR[3] = {16, 16, 8};
+    static constexpr int colW[4] = {16, 32, 16, 16};
+    static constexpr int colR[4] = {16, 16, 8, 32};
     static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
     static constexpr int p3R[14] = {32, 32, 32, 32, 32, 16, 32, 32, 32, 32, 32, 32, 32, 32};
     static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
@@ -37,8 +37,8 @@ template <> struct VariantTable<float> {
 };
 template <> struct VariantTable<double> {
     static constexpr int BUD = 16;
-    static constexpr int colW[3] = {8, 16, 8};
-    static constexpr int colR[3] = {8, 8, 16};
+    static constexpr int colW[4] = {8, 16, 8, 8};
+    static constexpr int colR[4] = {8, 8, 16, 32};
     static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
     static constexpr int p3R[14] = {16, 16, 16, 16, 16, 8, 16, 16, 16, 16, 16, 16, 16, 16};
     static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
@@ -50,13 +50,13 @@ __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
 }
 __host__ __device__ constexpr int at_least_32(int t) { return t < 32 ? 32 : t; }
 
-// Column variants 0..2 load their input with the threads; 3..5 are the same
+// Column variants 0..3 load their input with the threads; 4..7 are the same
 // shapes fed by bulk copies of the tile's input rows.
 template <typename real, int N, int V> struct ColShape {
     typedef VariantTable<real> VT;
-    static constexpr int W = VT::colW[V % 3];
-    static constexpr int RC = VT::colR[V % 3];
-    static constexpr bool BULK = V >= 3;
+    static constexpr int W = VT::colW[V % 4];
+    static constexpr int RC = VT::colR[V % 4];
+    static constexpr bool BULK = V >= 4;
     static constexpr int T = at_least_32(raw_threads(N, W, VT::BUD));
     typedef typename CT<real>::t cplx;
     static constexpr size_t smem = sizeof(cplx) * (size_t)(N + N * W);
