@@ -118,7 +118,8 @@ def _tg_reference_modes(orc, nu):
 
 @pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (1024, 0)])
 def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
-    # the bench's launch configuration; TG's RHS is known mode by mode from 8^3
+    # the bench's launch configuration (autotuned plan); TG's RHS is known
+    # mode by mode from 8^3
     nu = 1.0 / 4000
     modes = _tg_reference_modes(orc, nu)
     cd = torch.complex64 if dtype == 0 else torch.complex128
@@ -126,6 +127,7 @@ def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
     y = torch.empty_like(x)
     torch.cuda.synchronize()
     with dns.Solver(N, nu, 1e-3, dtype) as s:
+        dns.dns_autotune(s.h)
         s.rhs(x, y)
     scale = float(N) ** 3
     for (kx, ky, kz), v in modes.items():
@@ -137,13 +139,53 @@ def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
 
 @pytest.mark.slow
 def test_rhs_512_random_full_field(dns, orc):
-    # full 512^3 comparison in the bench's configuration (FP32)
+    # full 512^3 comparison in the bench's configuration (FP32, autotuned plan)
     uh = inputs.random_isotropic(512, seed=77, k0=4.0)
     ref = orc.rhs(uh, 1.0 / 4000)
     with dns.Solver(512, 1.0 / 4000, 1e-3, dns.DNS_F32) as s:
+        dns.dns_autotune(s.h)
         got = s.rhs(uh.astype(np.complex64))
     del uh
     assert rel(got, ref) < TOL[0]
+
+
+@pytest.mark.slow
+def test_rhs_1024_random_invariants(dns):
+    # 1024^3 is beyond the oracle's host memory, so the autotuned FP32 path is
+    # checked on properties every exact right-hand side has: it is solenoidal
+    # (k . dU = 0) and the nonlinear term moves no energy, so
+    # sum_k w Re(conj(u) . dU) = -nu sum_k w |k|^2 |u|^2 (w = half-spectrum weight).
+    # The field is a random 512^3 one embedded in the 1024^3 spectrum.
+    N, M, nu = 1024, 512, 1.0 / 4000
+    small = torch.from_numpy(inputs.random_isotropic(M, seed=78, k0=4.0).astype(np.complex64))
+    K = (M - 1) // 3
+    x = torch.zeros((3, N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+    idx = torch.cat([torch.arange(0, K + 1), torch.arange(-K, 0)])
+    ig = (idx % N).cuda()
+    x[:, ig[:, None], ig[None, :], : K + 1] = small[:, idx[:, None] % M, idx[None, :] % M, : K + 1].cuda()
+    del small
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    with dns.Solver(N, nu, 1e-3, dns.DNS_F32) as s:
+        dns.dns_autotune(s.h)
+        s.rhs(x, y)
+    k1 = torch.fft.fftfreq(N, 1.0 / N, device="cuda", dtype=torch.float64)
+    kz = torch.arange(N // 2 + 1, device="cuda", dtype=torch.float64)
+    w = torch.full_like(kz, 2.0)
+    w[0] = w[-1] = 1.0
+    div, dmag, rate, visc, scale = 0.0, 0.0, 0.0, 0.0, 0.0
+    for i in range(N):  # one kx plane at a time keeps the temporaries small
+        u, d = x[:, i].to(torch.complex128), y[:, i].to(torch.complex128)
+        kx = k1[i]
+        kd = kx * d[0] + k1[:, None] * d[1] + kz[None, :] * d[2]
+        k2 = kx * kx + k1[:, None] ** 2 + kz[None, :] ** 2
+        div = max(div, float(kd.abs().max()))
+        dmag = max(dmag, float((k2.sqrt() * d.abs().amax(0)).max()))
+        rate += float((w * (u.conj() * d).real.sum(0)).sum())
+        visc += float((w * k2 * (u.abs() ** 2).sum(0)).sum())
+        scale += float((w * (u.abs() * d.abs()).sum(0)).sum())
+    assert div < 1e-5 * dmag
+    assert abs(rate + nu * visc) < 1e-5 * scale
 
 
 # ---------------------------------------------------------------- time stepping
