@@ -747,23 +747,24 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
 }
 
 // ------------------------------------------------------------------- P5
+// Classical RK4 stage update of element e from this stage's right-hand side
+// du; u0, u1 are the step-start state and the accumulator at e, loaded by
+// the caller (before any store, so every load of a mode is in flight at
+// once).  Returns the next stage input (field type): what the next P1
+// transforms.
 template <typename real, typename acc>
-__device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real, acc> &a, long long m, int comp,
-                                                          long long sS, typename CT<real>::t du) {
-    // returns the next stage input (field type): the value the next P1 transforms
+__device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real, acc> &a, long long e,
+                                                          typename CT<real>::t du, typename CT<acc>::t u0,
+                                                          typename CT<acc>::t u1) {
     typedef typename CT<real>::t cplx;
     typedef typename CT<acc>::t cacc;
-    const long long e = comp * sS + m;
     if (a.stage < 0) {
         a.dU[e] = cmk<cacc>((acc)du.x, (acc)du.y);
         return du;
     }
     const acc dx = (acc)du.x, dy = (acc)du.y;
     const acc adt = (acc)a.adt, bdt = (acc)a.bdt;
-    cacc u0, u1;
-    if (a.stage < 3) u0 = a.U0[e];
     if (a.stage == 0) u1 = u0;
-    else u1 = a.U1[e];
     u1.x += adt * dx;
     u1.y += adt * dy;
     cplx next;
@@ -786,16 +787,11 @@ __device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real,
 //   s = 2: u1 += (dt/3) E1 k,          next = E2 u0 + dt E1 k
 //   s = 3: u1 += (dt/6) k  -> the new step-start state.
 template <typename real, typename acc>
-__device__ __forceinline__ typename CT<real>::t rk_update_if(const UpdateArgs<real, acc> &a, long long m, int comp,
-                                                             long long sS, typename CT<real>::t du, acc e1,
-                                                             acc e2) {
+__device__ __forceinline__ typename CT<real>::t rk_update_if(const UpdateArgs<real, acc> &a, long long e,
+                                                             typename CT<real>::t du, typename CT<acc>::t u0,
+                                                             typename CT<acc>::t u1, acc e1, acc e2) {
     typedef typename CT<real>::t cplx;
-    typedef typename CT<acc>::t cacc;
-    const long long e = comp * sS + m;
     const acc dx = (acc)du.x, dy = (acc)du.y, dt = (acc)a.dt;
-    cacc u0, u1;
-    if (a.stage < 3) u0 = a.U0[e];
-    if (a.stage > 0) u1 = a.U1[e];
     cplx next;
     if (a.stage == 0) {
         const acc c = (dt / (acc)6) * e2;
@@ -892,27 +888,45 @@ __device__ __forceinline__ void p5_mode_update(const Geo &g, const UpdateArgs<re
         args.dU[2 * sS + m] = cmk<cacc>(n2.x, n2.y);
         return;
     }
+    // every load of the mode before any store (the output arrays may alias
+    // nothing the compiler can prove, so loads after a store would wait)
+    const bool ifrk = args.ifrk && args.stage >= 0;
+    cplx v[3];          // stage input (viscous term of classical RK4)
+    cacc s0[3], s1[3];  // step-start state and accumulator
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = cmk<cplx>(0.0, 0.0);
+        s0[c] = s1[c] = cmk<cacc>(0.0, 0.0);
+        if (!ifrk) v[c] = args.U[c * sS + m];
+        if (args.stage >= 0 && args.stage < 3) s0[c] = args.U0[c * sS + m];
+        if (args.stage > 0) s1[c] = args.U1[c * sS + m];
+    }
     const real kx = (real)compact_to_k(ix, g.K), ky = (real)compact_to_k(iy, g.K), kzr = (real)kz;
     const real k2 = kx * kx + ky * ky + kzr * kzr;
     const real inv = k2 > 0 ? (real)1 / k2 : (real)0;
     const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
     const real dim = (kx * n0.y + ky * n1.y + kzr * n2.y) * inv;
-    const cplx u0 = args.U[m], u1 = args.U[sS + m], u2 = args.U[2 * sS + m];
     cplx x0, x1, x2;
-    if (args.ifrk && args.stage >= 0) {
+    if (ifrk) {
         // integrating factor: the stage value is the projected nonlinear term
         // alone; the viscous decay enters through E1 = exp(-nu k^2 dt/2),
         // E2 = exp(-nu k^2 dt), evaluated in the accumulator precision
         const acc L = (acc)nu * (acc)k2;
         const acc e1 = exp(-L * (acc)(0.5 * args.dt)), e2 = exp(-L * (acc)args.dt);
-        x0 = rk_update_if<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre, n0.y - kx * dim), e1, e2);
-        x1 = rk_update_if<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre, n1.y - ky * dim), e1, e2);
-        x2 = rk_update_if<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre, n2.y - kzr * dim), e1, e2);
+        x0 = rk_update_if<real, acc>(args, m, cmk<cplx>(n0.x - kx * dre, n0.y - kx * dim), s0[0], s1[0], e1, e2);
+        x1 = rk_update_if<real, acc>(args, sS + m, cmk<cplx>(n1.x - ky * dre, n1.y - ky * dim), s0[1], s1[1], e1,
+                                     e2);
+        x2 = rk_update_if<real, acc>(args, 2 * sS + m, cmk<cplx>(n2.x - kzr * dre, n2.y - kzr * dim), s0[2], s1[2],
+                                     e1, e2);
     } else {
         const real vk = nu * k2;
-        x0 = rk_update<real, acc>(args, m, 0, sS, cmk<cplx>(n0.x - kx * dre - vk * u0.x, n0.y - kx * dim - vk * u0.y));
-        x1 = rk_update<real, acc>(args, m, 1, sS, cmk<cplx>(n1.x - ky * dre - vk * u1.x, n1.y - ky * dim - vk * u1.y));
-        x2 = rk_update<real, acc>(args, m, 2, sS, cmk<cplx>(n2.x - kzr * dre - vk * u2.x, n2.y - kzr * dim - vk * u2.y));
+        x0 = rk_update<real, acc>(args, m, cmk<cplx>(n0.x - kx * dre - vk * v[0].x, n0.y - kx * dim - vk * v[0].y),
+                                  s0[0], s1[0]);
+        x1 = rk_update<real, acc>(args, sS + m,
+                                  cmk<cplx>(n1.x - ky * dre - vk * v[1].x, n1.y - ky * dim - vk * v[1].y), s0[1], s1[1]);
+        x2 = rk_update<real, acc>(args, 2 * sS + m,
+                                  cmk<cplx>(n2.x - kzr * dre - vk * v[2].x, n2.y - kzr * dim - vk * v[2].y), s0[2],
+                                  s1[2]);
     }
     if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
         cplx ox, oy, oz;
