@@ -309,14 +309,22 @@ __device__ __forceinline__ int radd(int n) { return n + (n >> 4); }
 // multiplies input r by w^(r k TWS), k = j mod Ns; neighbouring items read
 // entries r k TWS apart in the N-entry table, which puts many lanes of a warp
 // on one shared-memory bank for the larger r.  The table of stage s instead
-// stores those factors as [k][r - 1] (Ns (R - 1) entries), so lanes read
-// R - 1 entries apart: an odd stride, free of bank conflicts.  The tables of
-// all stages follow each other; twt_size rounds their total up to even so
-// what follows stays 16-byte aligned.
+// holds, per k, the factors of a split r = R1 a + b: w^(b k TWS) for
+// b = 1..R1-1 and w^(R1 a k TWS) for a = 1..R/R1-1 (radix 32: 8 x 4, 16:
+// 4 x 4, smaller radices unsplit), each factor one product away; rows are
+// padded to an odd length, so a warp's lanes read an odd stride apart (free
+// of bank conflicts) and a radix-32 item reads 10 entries instead of 31.
+// The tables of all stages follow each other; twt_size rounds their total
+// up to even so what follows stays 16-byte aligned.
+__host__ __device__ constexpr int twt_r1(int R) { return R == 32 ? 8 : (R == 16 ? 4 : R); }
+__host__ __device__ constexpr int twt_row(int R) {
+    const int e = (twt_r1(R) - 1) + (R / twt_r1(R) - 1);
+    return e % 2 ? e : e + 1;
+}
 __host__ __device__ constexpr int twt_offset(int N, int MAXR, int S, bool rev = false) {
     FftPlan p = plan_of(N, MAXR, rev);
     int off = 0;
-    for (int s = 1; s < S && s < p.nst; ++s) off += p.ns[s] * (p.r[s] - 1);
+    for (int s = 1; s < S && s < p.nst; ++s) off += p.ns[s] * twt_row(p.r[s]);
     return off;
 }
 __host__ __device__ constexpr int twt_size(int N, int MAXR, bool rev = false) {
@@ -332,11 +340,30 @@ __device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg) {
     constexpr FftPlan P = plan_of(N, MAXR, REV);
     if constexpr (S < P.nst) {
         constexpr int R = P.r[S], Ns = P.ns[S], TWS = N / (Ns * R), off = twt_offset(N, MAXR, S, REV);
-        for (int e = threadIdx.x; e < Ns * (R - 1); e += blockDim.x) {
-            const int k = e / (R - 1), r = e % (R - 1) + 1;
+        constexpr int R1 = twt_r1(R), ROW = twt_row(R);
+        for (int e = threadIdx.x; e < Ns * ROW; e += blockDim.x) {
+            const int k = e / ROW, i = e % ROW;
+            int r = 0;  // padding entries repeat w^0
+            if (i < R1 - 1) r = i + 1;
+            else if (i < R1 - 1 + R / R1 - 1) r = R1 * (i - (R1 - 1) + 1);
             twt[off + e] = twg[r * k * TWS];
         }
         build_twt<cplx, N, MAXR, REV, S + 1>(twt, twg);
+    }
+}
+// The R - 1 twiddles w^(r k TWS), r = 1..R-1, of one work item from its row
+// tk of a stage table (w[0] is left unset).
+template <int R, typename cplx> __device__ __forceinline__ void stage_twiddles(const cplx *tk, cplx (&w)[R]) {
+    constexpr int R1 = twt_r1(R), R2 = R / R1;
+    cplx wb[R1], wa[R2];
+#pragma unroll
+    for (int b = 1; b < R1; ++b) wb[b] = tk[b - 1];
+#pragma unroll
+    for (int a = 1; a < R2; ++a) wa[a] = tk[R1 - 1 + a - 1];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+        const int a = r / R1, b = r % R1;
+        w[r] = a == 0 ? wb[b] : (b == 0 ? wa[a] : cmul(wa[a], wb[b]));
     }
 }
 
@@ -377,13 +404,19 @@ struct RowFFT {
                 }
                 if constexpr (!first) {
                     const int k = j % Ns;
-                    const cplx *tk = tw + N + (REVP ? twt_size(N, MAXR) : 0) + twt_offset(N, MAXR, S, REVP) +
-                                     k * (R - 1) - 1;
+                    cplx w[R];
+                    if constexpr (TWT) {
+                        stage_twiddles<R>(tw + N + (REVP ? twt_size(N, MAXR) : 0) + twt_offset(N, MAXR, S, REVP) +
+                                              k * twt_row(R),
+                                          w);
+                    } else {
+#pragma unroll
+                        for (int r = 1; r < R; ++r) w[r] = tw[r * k * TWS];
+                    }
 #pragma unroll
                     for (int r = 1; r < R; ++r) {
-                        cplx w = TWT ? tk[r] : tw[r * k * TWS];
-                        if (SIGN > 0) w.y = -w.y;
-                        v[q][r] = cmul(v[q][r], w);
+                        if (SIGN > 0) w[r].y = -w[r].y;
+                        v[q][r] = cmul(v[q][r], w[r]);
                     }
                 }
                 dft<R, SIGN>(v[q]);

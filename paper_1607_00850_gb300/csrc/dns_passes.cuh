@@ -292,18 +292,17 @@ __device__ __forceinline__ void p3_mid_fused(typename CT<real>::t *tile, const t
         const int idx = (int)threadIdx.x + q * T;
         if (Q * T == TOT || idx < TOT) {
             const int l = idx / NB, j = idx % NB;
-            cplx x2[R];
+            cplx x2[R], w[R];
+            stage_twiddles<R>(twl + j * twt_row(R), w);
+#pragma unroll
+            for (int r = 1; r < R; ++r) w[r].y = -w[r].y;  // inverse transform: conjugate twiddles
 #pragma unroll
             for (int p = 0; p < 3; ++p) {
                 cplx *xp = p == 0 ? va[q] : (p == 1 ? vb[q] : x2);
 #pragma unroll
                 for (int r = 0; r < R; ++r) xp[r] = tile[(p * L + l) * LDR + radd(j + r * NB)];
 #pragma unroll
-                for (int r = 1; r < R; ++r) {
-                    cplx w = twl[j * (R - 1) + r - 1];
-                    w.y = -w.y;  // inverse transform: conjugate twiddles
-                    xp[r] = cmul(xp[r], w);
-                }
+                for (int r = 1; r < R; ++r) xp[r] = cmul(xp[r], w[r]);
                 dft<R, +1>(xp);
             }
             // point z = j + r NB: (ux, uy), (uz, wx), (wy, wz) -> Nx + i Ny, Nz + 0i
