@@ -420,8 +420,9 @@ def les_closure_bench():
     from paper_1607_00850_gb300 import experiments
     r = experiments.les_bench(64)
     peak, src = bf16_peak()
-    r["roofline"] = {"bound": "tensor", "kernel": "k_conv (three layers)", "achieved": r["forward_tflops"],
-                     "peak": peak, "unit": "TFLOP/s", "frac": r["forward_tflops"] / peak, "peak_source": src}
+    best = max(r["forward_tflops"], r["forward_tflops_tcgen05"])
+    r["roofline"] = {"bound": "tensor", "kernel": "k_conv / k_conv_tc (three layers, faster engine)",
+                     "achieved": best, "peak": peak, "unit": "TFLOP/s", "frac": best / peak, "peak_source": src}
     return r
 
 

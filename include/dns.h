@@ -220,6 +220,17 @@ int dns_net_free(dns_net net);
 /* Number of FP32 parameters, in the order w1[32][9][27], b1[32],
  * w2[32][32][27], b2[32], w3[6][32][27], b3[6]. */
 long dns_net_param_count(void);
+/* Convolution engine of the network's layers (forward and input
+ * gradients): DNS_CONV_MMA_SYNC (default) runs warp-level BF16 MMAs with
+ * the weights staged in shared memory; DNS_CONV_TCGEN05 runs the
+ * fifth-generation tensor cores (accumulators in tensor memory, operands
+ * in shared memory, one thread issuing the MMAs of a 128-voxel tile).  Both
+ * compute the same layers (BF16 operands, FP32 accumulation); the second is
+ * the slower of the two on this network (N = 32 output channels) at 64^3.
+ * DNS_ERR_ARG for any other value. */
+enum dns_conv_engine { DNS_CONV_MMA_SYNC = 0, DNS_CONV_TCGEN05 = 1 };
+int dns_net_set_engine(dns_net net, int engine);
+int dns_net_get_engine(dns_net net, int *engine);
 int dns_net_get_params(dns_net net, float *host, long count);
 int dns_net_set_params(dns_net net, const float *host, long count);
 /* Scales used only when the network serves as an LES closure: the network

@@ -15,6 +15,7 @@
 #include "dns.h"
 #include "dns_internal.h"
 #include "dns_les.cuh"
+#include "dns_tc.cuh"
 
 #include <cuda_bf16.h>
 
@@ -208,6 +209,175 @@ static cudaError_t conv(int n, const __nv_bfloat16 *X, const __nv_bfloat16 *W, c
 template <int CIN, int COUT, int EPI> static cudaError_t conv_attr() {
     return cudaFuncSetAttribute(k_conv<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)conv_smem<CIN, COUT>());
+}
+
+// The same convolution on the fifth-generation tensor cores.  A block of
+// 4 warps owns M = 128 consecutive voxels; the layer's weights (27 taps x
+// CIN/16 K steps of COUT x 16 BF16, already in the core-matrix layout, see
+// k_pack_canonical) sit in shared memory for the whole block.  For each tap
+// the 128 threads gather their voxels' shifted activations (one row each,
+// cp.async 16-byte copies) into one of NS A buffers in the core-matrix
+// layout, NS - 2 taps ahead of the MMAs; one thread issues the tap's CIN/16
+// MMAs (M 128, N COUT, K 16) accumulating in tensor memory and commits them
+// to the buffer's mbarrier, and a buffer is refilled only after that commit
+// (the MMAs of two taps back, so the wait for them is normally free).
+// The accumulators are read back lane per voxel for the epilogues.  Every
+// wait is bounded; on expiry the block records kErrWaitTimeout in *err,
+// lets the issued MMAs finish (bounded) and frees its tensor memory.
+template <int CIN, int COUT> struct ConvTc {
+    static constexpr int KS = CIN / 16;          // K steps per tap
+    static constexpr int BT = COUT / 8 * 256;    // bytes of one B tile (COUT x 16)
+    static constexpr int BBYTES = 27 * KS * BT;  // all weights
+    static constexpr int ABYTES = KS * 4096;     // one tap of A (128 x CIN)
+    static constexpr int NS = 5;                 // A buffers (taps in flight)
+    static constexpr size_t smem = (size_t)BBYTES + NS * ABYTES;
+};
+
+// W[o][t][c] (GPU layout, BF16) -> tiles (t, kk) of COUT x 16 in the K-major
+// core-matrix layout: byte (o/8) 256 + (k/8) 128 + (o%8) 16 + (k%8) 2 of
+// tile t KS + kk, k = c - 16 kk.
+template <int CIN, int COUT>
+__global__ void k_pack_canonical(const __nv_bfloat16 *__restrict__ W, __nv_bfloat16 *__restrict__ Wc) {
+    typedef ConvTc<CIN, COUT> C;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= COUT * 27 * CIN) return;
+    const int o = e / (27 * CIN), t = (e / CIN) % 27, c = e % CIN;
+    const int kk = c / 16, k = c % 16;
+    const int byte = (t * C::KS + kk) * C::BT + (o / 8) * 256 + (k / 8) * 128 + (o % 8) * 16 + (k % 8) * 2;
+    Wc[byte / 2] = W[e];
+}
+
+__device__ __forceinline__ void cp_async16(void *dst_smem, const void *src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst_smem)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int PENDING> __device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(PENDING) : "memory");
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(128) k_conv_tc(int n, const __nv_bfloat16 *__restrict__ X,
+                                                 const __nv_bfloat16 *__restrict__ Wc,
+                                                 const float *__restrict__ bias, float *__restrict__ Z,
+                                                 __nv_bfloat16 *__restrict__ A, const float *__restrict__ Zp,
+                                                 int *err) {
+    typedef ConvTc<CIN, COUT> C;
+    constexpr int NS = C::NS;
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, COUT);
+    constexpr uint32_t TCOLS = 32;
+    static_assert(COUT == 16 || COUT == 32, "one or two 16-column accumulator loads");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *sB = smem_raw;
+    unsigned char *sA = smem_raw + C::BBYTES;
+    __shared__ __align__(8) uint64_t bar[NS];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const long long v = (long long)blockIdx.x * 128 + tid;  // this thread's voxel = row of the M tile
+    const int z = (int)(v % n), y = (int)((v / n) % n), x = (int)(v / ((long long)n * n));
+    // this thread's row in an A buffer (chunk c of 8 channels at + (c/2) 4096 + (c%2) 128)
+    unsigned char *arow = sA + (tid / 8) * 256 + (tid % 8) * 16;
+    auto gather = [&](int t) {  // cp.async of tap t into buffer t % NS, one commit group
+        const __nv_bfloat16 *src = X + nbr(n, x, y, z, t) * CIN;
+        unsigned char *dst = arow + (t % NS) * C::ABYTES;
+#pragma unroll
+        for (int c = 0; c < CIN / 8; ++c) cp_async16(dst + (c / 2) * 4096 + (c % 2) * 128, src + 8 * c);
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int t = 0; t < NS - 2; ++t) gather(t);
+    for (int e = tid; e < C::BBYTES / 16; e += 128)
+        reinterpret_cast<uint4 *>(sB)[e] = reinterpret_cast<const uint4 *>(Wc)[e];
+    if (tid == 0) {
+#pragma unroll
+        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+        s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TCOLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t taddr = tmem_base;
+    int issued = -1;  // last tap whose MMAs were committed (thread 0)
+    for (int t = 0; t < 27; ++t) {
+        // refill buffer (t + NS - 2) % NS, last read by the MMAs of tap t - 2
+        const int tn = t + NS - 2;
+        if (tn < 27) {
+            if (t >= 2) {
+                if (tid == 0) s_ok = mbar_wait_bounded(&bar[(t - 2) % NS], ((t - 2) / NS) & 1) ? 1 : 0;
+                __syncthreads();
+                if (!s_ok) break;
+            }
+            gather(tn);
+        } else {
+            cp_async_commit();  // an empty group keeps the count of pending groups fixed
+        }
+        cp_async_wait<NS - 2>();  // this thread's copies of tap t have landed
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const unsigned char *a = sA + (t % NS) * C::ABYTES;
+#pragma unroll
+            for (int kk = 0; kk < C::KS; ++kk)
+                tc::mma_bf16(taddr, tc::smem_desc(a + kk * 4096, 128, 256),
+                             tc::smem_desc(sB + (t * C::KS + kk) * C::BT, 128, 256), IDESC, t > 0 || kk > 0);
+            tc::commit(&bar[t % NS]);
+            issued = t;
+        }
+    }
+    cp_async_wait<0>();
+    if (tid == 0) {  // the commit of the last issued tap covers every earlier MMA
+        const bool done = issued < 0 || mbar_wait_bounded(&bar[issued % NS], (issued / NS) & 1);
+        if (!done || !s_ok || issued != 26) {
+            s_ok = 0;
+            record_error(err, kErrWaitTimeout);
+        }
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (s_ok) {
+        float acc[COUT];
+        tc::ld16(taddr + ((uint32_t)(32 * warp) << 16), *reinterpret_cast<float(*)[16]>(acc));
+        if constexpr (COUT == 32)
+            tc::ld16(taddr + ((uint32_t)(32 * warp) << 16) + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+#pragma unroll
+        for (int o = 0; o < COUT; o += 2) {
+            float y0 = acc[o], y1 = acc[o + 1];
+            if (bias) {
+                y0 += bias[o];
+                y1 += bias[o + 1];
+            }
+            if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
+                *reinterpret_cast<float2 *>(Z + v * COUT + o) = make_float2(y0, y1);
+            }
+            if constexpr (EPI == EPI_HIDDEN) {
+                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) = __floats2bfloat162_rn(gelu_f(y0), gelu_f(y1));
+            }
+            if constexpr (EPI == EPI_DGRAD) {
+                const float2 zp = *reinterpret_cast<const float2 *>(Zp + v * COUT + o);
+                *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
+                    __floats2bfloat162_rn(y0 * gelu_d(zp.x), y1 * gelu_d(zp.y));
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(taddr, TCOLS);
+}
+
+template <int CIN, int COUT, int EPI>
+static cudaError_t conv_tc(int n, const __nv_bfloat16 *X, const __nv_bfloat16 *Wc, const float *bias, float *Z,
+                           __nv_bfloat16 *A, const float *Zp, int *err, cudaStream_t st) {
+    const long long V = (long long)n * n * n;
+    k_conv_tc<CIN, COUT, EPI><<<(unsigned)(V / 128), 128, ConvTc<CIN, COUT>::smem, st>>>(n, X, Wc, bias, Z, A, Zp,
+                                                                                          err);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int EPI> static cudaError_t conv_tc_attr() {
+    return cudaFuncSetAttribute(k_conv_tc<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)ConvTc<CIN, COUT>::smem);
 }
 
 // Weight gradient partials: block (chunk, tap) accumulates
@@ -412,8 +582,11 @@ struct dns_net_ctx {
     float *p = nullptr, *m = nullptr, *v = nullptr;
     float *gw1 = nullptr, *gw2 = nullptr, *gw3 = nullptr, *gb = nullptr;  // GPU-layout weight grads; bias grads
     long step = 0;
-    // BF16 packed weights
+    // BF16 packed weights, and the same in the tensor-core operand layout
     __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2f = nullptr, *W3f = nullptr;
+    __nv_bfloat16 *W1c = nullptr, *W2c = nullptr, *W3c = nullptr, *W2fc = nullptr, *W3fc = nullptr;
+    int *err = nullptr;  // device status word of the convolutions' bounded waits
+    int engine = 0;      // convolution engine: DNS_CONV_MMA_SYNC or DNS_CONV_TCGEN05
     // activations for one sample
     __nv_bfloat16 *X0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY3 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Y3 = nullptr, *wpart = nullptr;
@@ -430,8 +603,9 @@ static const long OFF_W1 = 0, OFF_B1 = OFF_W1 + NET_W1, OFF_W2 = OFF_B1 + NET_B1
 
 static void net_release(dns_net_ctx *c) {
     if (!c) return;
-    void *bufs[] = {c->p, c->m, c->v, c->gw1, c->gw2, c->gw3, c->gb, c->W1, c->W2, c->W3, c->W2f, c->W3f, c->X0,
-                    c->A1, c->A2, c->dY3, c->dZ2, c->dZ1, c->Z1, c->Z2, c->Y3, c->wpart, c->lpart, c->lsum};
+    void *bufs[] = {c->p,   c->m,   c->v,    c->gw1,  c->gw2,  c->gw3, c->gb,  c->W1,  c->W2,    c->W3,
+                    c->W2f, c->W3f, c->W1c,  c->W2c,  c->W3c,  c->W2fc, c->W3fc, c->err, c->X0,   c->A1,
+                    c->A2,  c->dY3, c->dZ2,  c->dZ1,  c->Z1,   c->Z2,  c->Y3,  c->wpart, c->lpart, c->lsum};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hostd) cudaFreeHost(c->hostd);
@@ -443,14 +617,31 @@ static cudaError_t net_pack(dns_net_ctx *c) {
     k_pack_weights<<<nblk(32 * 27 * 16), 256, 0, c->stream>>>(c->p + OFF_W1, 32, 9, 32, 16, c->W1, nullptr);
     k_pack_weights<<<nblk(32 * 27 * 32), 256, 0, c->stream>>>(c->p + OFF_W2, 32, 32, 32, 32, c->W2, c->W2f);
     k_pack_weights<<<nblk(OUTP * 27 * 32), 256, 0, c->stream>>>(c->p + OFF_W3, 6, 32, OUTP, 32, c->W3, c->W3f);
+    k_pack_canonical<16, 32><<<nblk(32 * 27 * 16), 256, 0, c->stream>>>(c->W1, c->W1c);
+    k_pack_canonical<32, 32><<<nblk(32 * 27 * 32), 256, 0, c->stream>>>(c->W2, c->W2c);
+    k_pack_canonical<32, OUTP><<<nblk(OUTP * 27 * 32), 256, 0, c->stream>>>(c->W3, c->W3c);
+    k_pack_canonical<32, 32><<<nblk(32 * 27 * 32), 256, 0, c->stream>>>(c->W2f, c->W2fc);
+    k_pack_canonical<OUTP, 32><<<nblk(32 * 27 * OUTP), 256, 0, c->stream>>>(c->W3f, c->W3fc);
     return cudaGetLastError();
 }
 
 // forward of one sample already in X0; leaves Z1, A1, Z2, A2, Y3
+// One convolution layer on the network's engine; W is the GPU-layout
+// weight array, Wc the same in the tensor-core operand layout.
+template <int CIN, int COUT, int EPI>
+static cudaError_t conv_layer(dns_net_ctx *c, const __nv_bfloat16 *X, const __nv_bfloat16 *W,
+                              const __nv_bfloat16 *Wc, const float *bias, float *Z, __nv_bfloat16 *A, const float *Zp,
+                              cudaStream_t st) {
+    if (c->engine == DNS_CONV_TCGEN05) return conv_tc<CIN, COUT, EPI>(c->n, X, Wc, bias, Z, A, Zp, c->err, st);
+    return conv<CIN, COUT, EPI>(c->n, X, W, bias, Z, A, Zp, st);
+}
+
 static cudaError_t net_forward_x0(dns_net_ctx *c, cudaStream_t st) {
-    cudaError_t e = conv<16, 32, EPI_HIDDEN>(c->n, c->X0, c->W1, c->p + OFF_B1, c->Z1, c->A1, nullptr, st);
-    if (e == cudaSuccess) e = conv<32, 32, EPI_HIDDEN>(c->n, c->A1, c->W2, c->p + OFF_B2, c->Z2, c->A2, nullptr, st);
-    if (e == cudaSuccess) e = conv<32, OUTP, EPI_OUT>(c->n, c->A2, c->W3, nullptr, c->Y3, nullptr, nullptr, st);
+    cudaError_t e = conv_layer<16, 32, EPI_HIDDEN>(c, c->X0, c->W1, c->W1c, c->p + OFF_B1, c->Z1, c->A1, nullptr, st);
+    if (e == cudaSuccess)
+        e = conv_layer<32, 32, EPI_HIDDEN>(c, c->A1, c->W2, c->W2c, c->p + OFF_B2, c->Z2, c->A2, nullptr, st);
+    if (e == cudaSuccess)
+        e = conv_layer<32, OUTP, EPI_OUT>(c, c->A2, c->W3, c->W3c, nullptr, c->Y3, nullptr, nullptr, st);
     return e;
 }
 
@@ -486,15 +677,15 @@ static cudaError_t net_backward(dns_net_ctx *c, const float *tau) {
     k_wgrad<32, OUTP><<<wg, 256, 0, c->stream>>>(c->n, c->dY3, c->A2, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
     k_wgrad_reduce<<<nblk(27 * OUTP * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, OUTP, 32, c->gw3);
     k_colsum<<<OUTP, 256, 0, c->stream>>>(c->dY3, V, OUTP, 6, c->gb + 64);
-    if ((e = conv<OUTP, 32, EPI_DGRAD>(c->n, c->dY3, c->W3f, nullptr, nullptr, c->dZ2, c->Z2, c->stream)) !=
-        cudaSuccess)
+    if ((e = conv_layer<OUTP, 32, EPI_DGRAD>(c, c->dY3, c->W3f, c->W3fc, nullptr, nullptr, c->dZ2, c->Z2,
+                                             c->stream)) != cudaSuccess)
         return e;
     // layer 2
     k_wgrad<32, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ2, c->A1, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
     k_wgrad_reduce<<<nblk(27 * 32 * 32), 256, 0, c->stream>>>(c->wpart, c->nchunk, 32, 32, c->gw2);
     k_colsum<<<32, 256, 0, c->stream>>>(c->dZ2, V, 32, 32, c->gb + 32);
-    if ((e = conv<32, 32, EPI_DGRAD>(c->n, c->dZ2, c->W2f, nullptr, nullptr, c->dZ1, c->Z1, c->stream)) !=
-        cudaSuccess)
+    if ((e = conv_layer<32, 32, EPI_DGRAD>(c, c->dZ2, c->W2f, c->W2fc, nullptr, nullptr, c->dZ1, c->Z1,
+                                           c->stream)) != cudaSuccess)
         return e;
     // layer 1
     k_wgrad<16, 32><<<wg, 256, 0, c->stream>>>(c->n, c->dZ1, c->X0, c->wpart, (int)((V + c->nchunk - 1) / c->nchunk));
@@ -508,6 +699,14 @@ static cudaError_t net_backward(dns_net_ctx *c, const float *tau) {
         cudaError_t e_ = (call);       \
         if (e_ != cudaSuccess) return DNS_ERR_CUDA; \
     } while (0)
+
+// After the network's stream has drained: DNS_ERR_TIMEOUT if a convolution
+// gave up one of its bounded waits (the status stays set).
+static int net_status(dns_net_ctx *c) {
+    int v = 0;
+    if (cudaMemcpy(&v, c->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return DNS_ERR_CUDA;
+    return v ? DNS_ERR_TIMEOUT : DNS_OK;
+}
 
 extern "C" {
 
@@ -539,6 +738,12 @@ int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *o
     al((void **)&c->W3, 2 * OUTP * 27 * 32);
     al((void **)&c->W2f, 2 * 32 * 27 * 32);
     al((void **)&c->W3f, 2 * 32 * 27 * OUTP);
+    al((void **)&c->W1c, 2 * 32 * 27 * 16);
+    al((void **)&c->W2c, 2 * 32 * 27 * 32);
+    al((void **)&c->W3c, 2 * OUTP * 27 * 32);
+    al((void **)&c->W2fc, 2 * 32 * 27 * 32);
+    al((void **)&c->W3fc, 2 * 32 * 27 * OUTP);
+    al((void **)&c->err, sizeof(int));
     al((void **)&c->X0, 2 * V * 16);
     al((void **)&c->A1, 2 * V * 32);
     al((void **)&c->A2, 2 * V * 32);
@@ -581,6 +786,9 @@ int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *o
     if (cudaMemcpy(c->p, h.data(), sizeof(float) * NET_PARAMS, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->m, 0, sizeof(float) * NET_PARAMS) != cudaSuccess ||
         cudaMemset(c->v, 0, sizeof(float) * NET_PARAMS) != cudaSuccess || net_pack(c) != cudaSuccess ||
+        cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess || conv_tc_attr<16, 32, EPI_HIDDEN>() != cudaSuccess ||
+        conv_tc_attr<32, 32, EPI_HIDDEN>() != cudaSuccess || conv_tc_attr<32, OUTP, EPI_OUT>() != cudaSuccess ||
+        conv_tc_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess || conv_tc_attr<32, 32, EPI_DGRAD>() != cudaSuccess ||
         conv_attr<16, 32, EPI_HIDDEN>() != cudaSuccess || conv_attr<32, 32, EPI_HIDDEN>() != cudaSuccess ||
         conv_attr<32, OUTP, EPI_OUT>() != cudaSuccess || conv_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess ||
         conv_attr<32, 32, EPI_DGRAD>() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -599,6 +807,18 @@ int dns_net_free(dns_net net) {
 }
 
 long dns_net_param_count(void) { return NET_PARAMS; }
+
+int dns_net_set_engine(dns_net net, int engine) {
+    if (!net || (engine != DNS_CONV_MMA_SYNC && engine != DNS_CONV_TCGEN05)) return DNS_ERR_ARG;
+    net->engine = engine;
+    return DNS_OK;
+}
+
+int dns_net_get_engine(dns_net net, int *engine) {
+    if (!net || !engine) return DNS_ERR_ARG;
+    *engine = net->engine;
+    return DNS_OK;
+}
 
 int dns_net_set_closure_scaling(dns_net net, double in_scale, double out_scale) {
     if (!net || !(in_scale > 0.0) || !(out_scale > 0.0) || !std::isfinite(in_scale) || !std::isfinite(out_scale))
@@ -630,7 +850,7 @@ int dns_net_forward(dns_net net, const float *g, float *tau) {
     k_out_to_tau<<<nblk(6 * V), 256, 0, net->stream>>>(net->Y3, V, tau, 1.0f);
     NK(cudaGetLastError());
     NK(cudaStreamSynchronize(net->stream));
-    return DNS_OK;
+    return net_status(net);
 }
 
 int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count) {
@@ -667,7 +887,7 @@ int dns_net_gradients(dns_net net, const float *g, const float *tau, double *los
     }
     NK(cudaStreamSynchronize(net->stream));
     if (loss) *loss = net->hostd[0];
-    return DNS_OK;
+    return net_status(net);
 }
 
 int dns_net_train_step(dns_net net, int nsamples, const float *g, const float *tau, double lr, double *loss) {
@@ -711,7 +931,7 @@ int dns_net_train_step(dns_net net, int nsamples, const float *g, const float *t
     NK(cudaStreamSynchronize(net->stream));
     if (loss) *loss = net->hostd[0] / nsamples;
     (void)V;
-    return DNS_OK;
+    return net_status(net);
 }
 
 }  // extern "C"

@@ -60,6 +60,8 @@ SIGNATURES = {
     "dns_net_create": (_i, [_i, ctypes.c_ulonglong, _vp, ctypes.POINTER(_vp)]),
     "dns_net_free": (_i, [_vp]),
     "dns_net_param_count": (ctypes.c_long, []),
+    "dns_net_set_engine": (_i, [_vp, _i]),
+    "dns_net_get_engine": (_i, [_vp, ctypes.POINTER(_i)]),
     "dns_net_set_closure_scaling": (_i, [_vp, _d, _d]),
     "dns_net_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "dns_net_set_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
@@ -473,6 +475,19 @@ def dns_net_free(net: int) -> None:
 
 def dns_net_param_count() -> int:
     return int(load().dns_net_param_count())
+
+
+DNS_CONV_MMA_SYNC, DNS_CONV_TCGEN05 = 0, 1
+
+
+def dns_net_set_engine(net: int, engine: int) -> None:
+    _check(load().dns_net_set_engine(net, int(engine)), "dns_net_set_engine")
+
+
+def dns_net_get_engine(net: int) -> int:
+    v = ctypes.c_int()
+    _check(load().dns_net_get_engine(net, ctypes.byref(v)), "dns_net_get_engine")
+    return v.value
 
 
 def dns_net_get_params(net: int) -> np.ndarray:

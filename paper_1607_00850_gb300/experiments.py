@@ -253,7 +253,8 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
     """Cost of the learned closure on the GPU: the network forward on one n^3
     sample (flops = 2 n^3 27 (9*32 + 32*32 + 32*6), the contraction the
     tensor cores run; the input channels are padded to 16 and the output to
-    16 on the device, which is not counted), one Adam training step per
+    16 on the device, which is not counted) on both convolution engines (the
+    rest uses the default one), one Adam training step per
     sample, and one LES step at n^3 without a model, with Smagorinsky and
     with the learned closure, next to one DNS step at dns_N^3.  Times by CUDA
     events on the default stream (forward) and wall clock around
@@ -269,16 +270,24 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
         tau = torch.empty((6, n, n, n), device=dev)
         G = torch.randn((batch, 9, n, n, n), device=dev, generator=gen)
         T = torch.randn((batch, 6, n, n, n), device=dev, generator=gen)
-        for _ in range(3):
-            dns.dns_net_forward(net, g, tau)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            dns.dns_net_forward(net, g, tau)
-        b.record()
-        b.synchronize()
-        fwd = a.elapsed_time(b) / reps
+        def time_forward():
+            for _ in range(3):
+                dns.dns_net_forward(net, g, tau)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(reps):
+                dns.dns_net_forward(net, g, tau)
+            b.record()
+            b.synchronize()
+            return a.elapsed_time(b) / reps
+
+        dns.dns_net_set_engine(net, dns.DNS_CONV_TCGEN05)
+        fwd_tc = time_forward()
+        out["forward_ms_tcgen05"] = fwd_tc
+        out["forward_tflops_tcgen05"] = flops / (fwd_tc / 1e3) / 1e12
+        dns.dns_net_set_engine(net, dns.DNS_CONV_MMA_SYNC)
+        fwd = time_forward()
         out["forward_ms"] = fwd
         out["forward_tflops"] = flops / (fwd / 1e3) / 1e12
         dns.dns_net_train_step(net, batch, G, T, 1e-4)

@@ -83,10 +83,13 @@ def sample16(dns):
     return g / g.std(), tau / tau.std()
 
 
-def test_net_forward_matches_oracle(dns, orc, sample16):
+@pytest.mark.parametrize("engine", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_net_forward_matches_oracle(dns, orc, sample16, engine):
     g, _ = sample16
     net = dns.dns_net_create(16, seed=3)
     try:
+        dns.dns_net_set_engine(net, engine)
+        assert dns.dns_net_get_engine(net) == engine
         p = dns.dns_net_get_params(net)
         pb = p.copy()
         for k, (o, s) in enumerate([(0, 32 * 9 * 27), (32 * 9 * 27 + 32, 32 * 32 * 27),
@@ -101,10 +104,12 @@ def test_net_forward_matches_oracle(dns, orc, sample16):
         dns.dns_net_free(net)
 
 
-def test_net_gradients_match_oracle(dns, orc, sample16):
+@pytest.mark.parametrize("engine", [0, 1], ids=["mma_sync", "tcgen05"])
+def test_net_gradients_match_oracle(dns, orc, sample16, engine):
     g, t = sample16
     net = dns.dns_net_create(16, seed=4)
     try:
+        dns.dns_net_set_engine(net, engine)
         p = dns.dns_net_get_params(net)
         pb = p.copy()
         for o, s in [(0, 32 * 9 * 27), (32 * 9 * 27 + 32, 32 * 32 * 27), (32 * 9 * 27 + 64 + 32 * 32 * 27, 6 * 32 * 27)]:
@@ -221,3 +226,28 @@ def test_smagorinsky_dissipates(dns):
     with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
         with pytest.raises(dns.DnsError):
             dns.dns_les_set_smagorinsky(s.h, -0.1)
+
+
+@pytest.mark.parametrize("n", [32, 64])
+def test_conv_engines_agree(dns, n):
+    # both engines compute the same BF16 x BF16 -> FP32 layers; only the
+    # order of the FP32 accumulation differs
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    g = torch.randn((9, n, n, n), device="cuda", generator=gen)
+    outs = []
+    for engine in (0, 1):
+        net = dns.dns_net_create(n, seed=12)
+        try:
+            dns.dns_net_set_engine(net, engine)
+            tau = torch.empty((6, n, n, n), device="cuda")
+            dns.dns_net_forward(net, g, tau)
+            outs.append(tau.cpu().numpy())
+        finally:
+            dns.dns_net_free(net)
+    assert rel(outs[1], outs[0]) < 1e-2
+    with pytest.raises(dns.DnsError):
+        net = dns.dns_net_create(16, seed=1)
+        try:
+            dns.dns_net_set_engine(net, 2)
+        finally:
+            dns.dns_net_free(net)
