@@ -199,7 +199,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (nominal; no measured FP64 peak is ava
 PASS_NAMES = ["p1_xinv", "p2_yinv", "p3_z_cross", "p4_yfwd", "p5a_xfwd", "p5b_update"]
 
 
-def survey_step_bytes(N, dtype):
+def unpruned_step_bytes(N, dtype):
     """The unpruned reference byte model: 216 spectral-field passes per RK4
     step, one field F = N^2 (N/2+1) complex."""
     cr = 16 if dtype == 1 else 8
@@ -290,8 +290,8 @@ def run_ours(args, rank, world, local_rank):
                 "algorithmic_bytes_per_launch": avg_bytes[dom], "avg_launch_ms": dur,
                 "step_bytes_pruned": step_bytes,
                 "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
-                "step_bytes_216F_model": survey_step_bytes(N, 0),
-                "step_frac_216F_model": survey_step_bytes(N, 0) / (ms / args.steps / 1e3) / 1e9 / peak,
+                "step_bytes_216F_model": unpruned_step_bytes(N, 0),
+                "step_frac_216F_model": unpruned_step_bytes(N, 0) / (ms / args.steps / 1e3) / 1e9 / peak,
                 "pass_ms_per_launch": {names[i]: pass_ms[i] / launches for i in range(6)},
                 "pass_gbs": {names[i]: avg_bytes[i] / (pass_ms[i] / launches / 1e3) / 1e9 for i in range(6)},
                 "pass_share": {names[i]: pass_ms[i] / max(prof_total, 1e-9) for i in range(6)}}
@@ -399,7 +399,7 @@ def ensemble_bench(args, stream):
             "ms_per_step": ms / args.steps, "steps": args.steps,
             "step_bytes_pruned": step_bytes,
             "step_frac_pruned": step_bytes / (ms / args.steps / 1e3) / 1e9 / peak,
-            "step_frac_216F_model": sum(survey_step_bytes(n, 0) for n in Ns) / (ms / args.steps / 1e3) / 1e9 / peak,
+            "step_frac_216F_model": sum(unpruned_step_bytes(n, 0) for n in Ns) / (ms / args.steps / 1e3) / 1e9 / peak,
             "peak_source": src, "energy_min": float(E.min()), "energy_max": float(E.max())}
 
 
