@@ -82,6 +82,13 @@ def _log_spectrum_error(e: np.ndarray, ref: np.ndarray, kc: int) -> float:
     return float(np.sqrt(np.mean(np.log10(np.maximum(e[k], 1e-300) / ref[k]) ** 2)))
 
 
+def _shell_errors(e: np.ndarray, ref: np.ndarray, kc: int) -> tuple[float, float]:
+    """(max, mean) over shells 1..kc of |E(k)/E_ref(k) - 1|."""
+    k = np.arange(1, kc + 1)
+    r = np.abs(e[k] / ref[k] - 1.0)
+    return float(r.max()), float(r.mean())
+
+
 def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, k0: float = 4.0,
                 seeds: int = 40, snaps: int = 50, spinup: int = 100, stride: int = 1, epochs: int = 8,
                 batch: int = 8, lr: float = 1e-3, eval_steps: int = 500, eval_every: int = 50, cs: float = 0.17,
@@ -202,8 +209,10 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
                     hist["filtered_dns"].append({"step": done, "E": ref.energy()})
                     for m, s in zip(models, (a, sm, le)):
                         e = s.spectrum()
+                        mx, mean = _shell_errors(e, eref, kc)
                         hist[m].append({"step": done, "E": s.energy(),
-                                        "log_spectrum_err": _log_spectrum_error(e, eref, kc)})
+                                        "log_spectrum_err": _log_spectrum_error(e, eref, kc),
+                                        "shell_rel_err_max": mx, "shell_rel_err_mean": mean})
                     if done >= eval_steps:
                         final = {m: s.spectrum()[:kc + 2].tolist() for m, s in zip(models, (a, sm, le))}
                         final["filtered_dns"] = eref[:kc + 2].tolist()
@@ -347,6 +356,7 @@ def main(argv=None):
     q.add_argument("--batch", type=int, default=8)
     q.add_argument("--lr", type=float, default=1e-3)
     q.add_argument("--eval-steps", type=int, default=500)
+    q.add_argument("--seed0", type=int, default=5000)
     q.add_argument("--out", default=None, help="write the full report (JSON) here")
     args = p.parse_args(argv)
     if args.cmd == "les-bench":
@@ -357,7 +367,7 @@ def main(argv=None):
         dns.load()
         rep = les_closure(args.N, args.n, seeds=args.seeds, snaps=args.snaps, spinup=args.spinup,
                           stride=args.stride, epochs=args.epochs, batch=args.batch, lr=args.lr,
-                          eval_steps=args.eval_steps)
+                          eval_steps=args.eval_steps, seed0=args.seed0)
         if args.out:
             with open(args.out, "w") as f:
                 json.dump(rep, f)
