@@ -116,7 +116,20 @@ def _tg_reference_modes(orc, nu):
     return out
 
 
-@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (1024, 0)])
+@pytest.mark.parametrize("N", [128, 192, 384])
+def test_rhs_matches_oracle_larger_meshes_tuned(dns, orc, N):
+    # radix-2 and radix-3 meshes between the small cases and the benchmark,
+    # FP32 in the autotuned plan
+    nu = 1.0 / 2000
+    uh = inputs.random_isotropic(N, seed=300 + N, k0=4.0)
+    ref = orc.rhs(uh, nu)
+    with dns.Solver(N, nu, 1e-3, dns.DNS_F32) as s:
+        dns.dns_autotune(s.h)
+        got = s.rhs(uh.astype(np.complex64))
+    assert rel(got, ref) < TOL[0]
+
+
+@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (768, 0), (1024, 0)])
 def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
     # the bench's launch configuration (autotuned plan); TG's RHS is known
     # mode by mode from 8^3
