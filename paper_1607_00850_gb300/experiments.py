@@ -90,7 +90,7 @@ def _shell_errors(e: np.ndarray, ref: np.ndarray, kc: int) -> tuple[float, float
 
 
 def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, k0: float = 4.0,
-                seeds: int = 40, snaps: int = 50, spinup: int = 100, stride: int = 1, epochs: int = 8,
+                seeds: int = 40, snaps: int = 50, spinup: int = 100, stride: int = 10, epochs: int = 8,
                 batch: int = 8, lr: float = 1e-3, eval_steps: int = 500, eval_every: int = 50, cs: float = 0.17,
                 seed0: int = 5000, out=sys.stdout) -> dict:
     """Learned subgrid closure for an n^3 LES fed by sharp-cutoff filtered N^3
@@ -98,9 +98,11 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
 
     1. Training data: `seeds` random-phase fields (E(k) ~ k^4 exp(-2(k/k0)^2),
        unit energy), each spun up for `spinup` DNS steps, then `snaps`
-       snapshots `stride` steps apart; each snapshot gives the 9 filtered
-       velocity gradients and 6 subgrid stresses on the LES mesh.  All of it
-       stays in device memory.
+       snapshots `stride` steps apart (by default spanning the same stretch
+       of the decay as the a-posteriori run below, so the closure is not
+       asked to extrapolate to later states); each snapshot gives the 9
+       filtered velocity gradients and 6 subgrid stresses on the LES mesh.
+       All of it stays in device memory.
     2. Training: the inputs and targets are scaled to unit rms (the scales
        go into the closure); Adam on shuffled mini-batches for `epochs`
        passes; the loss on a held-out seed is reported per epoch.
@@ -351,7 +353,7 @@ def main(argv=None):
     q.add_argument("--seeds", type=int, default=40)
     q.add_argument("--snaps", type=int, default=50)
     q.add_argument("--spinup", type=int, default=100)
-    q.add_argument("--stride", type=int, default=1)
+    q.add_argument("--stride", type=int, default=10)
     q.add_argument("--epochs", type=int, default=8)
     q.add_argument("--batch", type=int, default=8)
     q.add_argument("--lr", type=float, default=1e-3)
