@@ -260,7 +260,7 @@ def test_trained_closure_gains_over_no_model(dns):
     from paper_1607_00850_gb300 import experiments
     # (240 training samples, 40 epochs: about 10 s; on three held-out seeds the
     # learned error was 0.21-0.31 of the no-model error)
-    rep = experiments.les_closure(N=128, n=32, nu=2e-3, dt=0.004, seeds=8, snaps=30, spinup=50, epochs=40,
+    rep = experiments.les_closure(N=128, n=32, nu=2e-3, dt=0.004, seeds=8, snaps=30, spinup=50, stride=1, epochs=40,
                                   batch=8, lr=2e-3, eval_steps=200, eval_every=100, seed0=6200, out=None)
     post = rep["a_posteriori"]
     assert rep["epochs"][-1]["val_loss"] < 0.6 * rep["epochs"][0]["val_loss"]
