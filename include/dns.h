@@ -16,9 +16,11 @@
  *  - Every function returns an int status (dns_status); nothing throws.
  *  - One handle is used by one host thread at a time.
  *  - The handle owns all device memory it needs; it is allocated by
- *    dns_init and released by dns_free.  Caller buffers are never retained:
+ *    dns_init and released by dns_free.  Caller buffers are not retained:
  *    the library copies in or out before returning (or, for device buffers,
- *    in stream order on the handle's stream).
+ *    in stream order on the handle's stream); the one exception is the
+ *    asynchronous host I/O, which uses the caller's host buffer until
+ *    dns_synchronize returns.
  *  - `on_device` = 1: the pointer is device memory (e.g. a torch CUDA
  *    tensor's data_ptr()); 0: host memory (pinned or pageable).
  *  - Spectral layout ("full"): uhat[3][N][N][N/2+1] complex, C order,
@@ -84,6 +86,29 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device);
  * set).  Synchronises the handle's stream. */
 int dns_get_velocity(dns_handle h, void *uhat, int on_device);
 
+/* Asynchronous host I/O, for streaming many fields through one handle
+ * (set, step, get, set, ...) with the host copies overlapping the steps of
+ * the neighbouring fields.  uhat is HOST memory in the full spectral layout
+ * above (page-locked memory lets the copies overlap; pageable memory is
+ * still correct).  Both calls only queue work and return at once.
+ *
+ * dns_set_velocity_async: the copy of uhat into an internal staging buffer
+ * runs on an internal copy stream as soon as the previous asynchronous set
+ * has been converted; the state is replaced (and its curl computed) on the
+ * handle's stream, after everything queued there before.  uhat must stay
+ * valid and unchanged until dns_synchronize returns.
+ *
+ * dns_get_velocity_async: the state as it is when the handle's stream
+ * reaches this call is converted into one of two staging buffers (taking
+ * turns) and copied to uhat on a second copy stream; uhat holds it once
+ * dns_synchronize has returned.
+ *
+ * The first call allocates three staging buffers of the full layout's size
+ * (counted by dns_device_bytes); DNS_ERR_OOM if they do not fit, the handle
+ * is then unchanged.  dns_synchronize waits for the copy streams too. */
+int dns_set_velocity_async(dns_handle h, const void *uhat);
+int dns_get_velocity_async(dns_handle h, void *uhat);
+
 /* One evaluation of the right-hand side of Eq. NSfinal on uhat_in (full
  * layout), written to duhat_out (full layout).  Leaves the state unchanged.
  * Synchronises the handle's stream. */
@@ -116,7 +141,8 @@ int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms);
 enum dns_integrator { DNS_RK4 = 0, DNS_IFRK4 = 1 };
 int dns_set_integrator(dns_handle h, int kind);
 
-/* Wait for the handle's queued work; reports device errors, and
+/* Wait for the handle's queued work (its stream and the copy streams of the
+ * asynchronous host I/O); reports device errors, and
  * DNS_ERR_TIMEOUT when a kernel gave up one of its bounded waits (a bulk
  * copy into shared memory that did not complete within one second; the
  * state is then not trustworthy and the status stays set). */

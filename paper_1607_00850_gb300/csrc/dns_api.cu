@@ -59,6 +59,13 @@ struct dns_ctx {
     int integrator = 0;             // DNS_RK4 or DNS_IFRK4
     dns::LesClosure *closure = nullptr;  // learned subgrid closure (LES handles), or nullptr
     void *Fext = nullptr;                // its forcing on the stored modes
+    // asynchronous host I/O (created on first use): a copy-in and a copy-out
+    // stream, one staging buffer in and two out (full spectral layout)
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    void *io_in = nullptr, *io_out[2] = {nullptr, nullptr};
+    cudaEvent_t in_copied = nullptr, in_free = nullptr, out_ready[2] = {nullptr, nullptr},
+                out_copied[2] = {nullptr, nullptr};
+    int out_slot = 0;
 };
 
 static thread_local cudaError_t g_last_cuda = cudaSuccess;
@@ -77,6 +84,8 @@ static thread_local cudaError_t g_last_cuda = cudaSuccess;
 static const double RK_A[4] = {1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0};
 static const double RK_B[3] = {0.5, 0.5, 1.0};
 
+static void drop_async_io(dns_ctx *h);
+
 static void release(dns_ctx *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -88,6 +97,7 @@ static void release(dns_ctx *h) {
     if (h->host) cudaFreeHost(h->host);
     if (h->closure) dns::les_closure_release(h->closure);
     if (h->Fext) cudaFree(h->Fext);
+    drop_async_io(h);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -445,7 +455,94 @@ static int poll_device_status(dns_ctx *h) {
 int dns_synchronize(dns_handle h) {
     if (!h) return DNS_ERR_ARG;
     CK(cudaStreamSynchronize(h->stream));
+    if (h->s_in) CK(cudaStreamSynchronize(h->s_in));
+    if (h->s_out) CK(cudaStreamSynchronize(h->s_out));
     return poll_device_status(h);
+}
+
+}  // extern "C"
+
+// Streams, events and staging buffers of the asynchronous host I/O, made on
+// first use; a failure leaves none of them behind.
+static void drop_async_io(dns_ctx *h) {
+    for (cudaStream_t *st : {&h->s_in, &h->s_out})
+        if (*st) {
+            cudaStreamSynchronize(*st);
+            cudaStreamDestroy(*st);
+            *st = nullptr;
+        }
+    for (cudaEvent_t *ev : {&h->in_copied, &h->in_free, &h->out_ready[0], &h->out_ready[1], &h->out_copied[0],
+                            &h->out_copied[1]})
+        if (*ev) {
+            cudaEventDestroy(*ev);
+            *ev = nullptr;
+        }
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    for (void **p : {&h->io_in, &h->io_out[0], &h->io_out[1]})
+        if (*p) {
+            cudaFree(*p);
+            h->bytes -= (long long)bytes;
+            *p = nullptr;
+        }
+}
+
+static int ensure_async_io(dns_ctx *h) {
+    if (h->io_out[1]) return DNS_OK;  // the last thing made: all of it exists
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    cudaError_t e = cudaSuccess;
+    for (cudaStream_t *st : {&h->s_in, &h->s_out})
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+    for (cudaEvent_t *ev : {&h->in_copied, &h->in_free, &h->out_ready[0], &h->out_ready[1], &h->out_copied[0],
+                            &h->out_copied[1]})
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        drop_async_io(h);
+        return DNS_ERR_CUDA;
+    }
+    for (void **p : {&h->io_in, &h->io_out[0], &h->io_out[1]}) {
+        const int rc = dev_alloc(h, p, bytes);
+        if (rc != DNS_OK) {
+            drop_async_io(h);
+            return rc;
+        }
+    }
+    return DNS_OK;
+}
+
+extern "C" {
+
+int dns_set_velocity_async(dns_handle h, const void *uhat) {
+    if (!h || !uhat) return DNS_ERR_ARG;
+    const int rc = ensure_async_io(h);
+    if (rc != DNS_OK) return rc;
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    // the staging buffer is free once the previous conversion has read it
+    CK(cudaStreamWaitEvent(h->s_in, h->in_free, 0));
+    CK(cudaMemcpyAsync(h->io_in, uhat, bytes, cudaMemcpyHostToDevice, h->s_in));
+    CK(cudaEventRecord(h->in_copied, h->s_in));
+    CK(cudaStreamWaitEvent(h->stream, h->in_copied, 0));
+    CK(full_to_state(h, h->io_in, h->U, h->U0));
+    CK(cudaEventRecord(h->in_free, h->stream));
+    CK(curl_box(h, 0));
+    return DNS_OK;
+}
+
+int dns_get_velocity_async(dns_handle h, void *uhat) {
+    if (!h || !uhat) return DNS_ERR_ARG;
+    const int rc = ensure_async_io(h);
+    if (rc != DNS_OK) return rc;
+    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
+    const int k = h->out_slot;
+    h->out_slot ^= 1;
+    // this slot's previous read-back (two calls ago) must have left it
+    CK(cudaStreamWaitEvent(h->stream, h->out_copied[k], 0));
+    CK(acc_to_full(h, h->U0, h->io_out[k]));
+    CK(cudaEventRecord(h->out_ready[k], h->stream));
+    CK(cudaStreamWaitEvent(h->s_out, h->out_ready[k], 0));
+    CK(cudaMemcpyAsync(uhat, h->io_out[k], bytes, cudaMemcpyDeviceToHost, h->s_out));
+    CK(cudaEventRecord(h->out_copied[k], h->s_out));
+    return DNS_OK;
 }
 
 int dns_set_velocity(dns_handle h, const void *uhat, int on_device) {

@@ -31,6 +31,8 @@ SIGNATURES = {
     "dns_set_velocity": (_i, [_vp, _vp, _i]),
     "dns_set_velocity_physical": (_i, [_vp, _vp, _i]),
     "dns_get_velocity": (_i, [_vp, _vp, _i]),
+    "dns_set_velocity_async": (_i, [_vp, _vp]),
+    "dns_get_velocity_async": (_i, [_vp, _vp]),
     "dns_rhs": (_i, [_vp, _vp, _vp, _i]),
     "dns_step": (_i, [_vp, _i]),
     "dns_step_profiled": (_i, [_vp, _i, _dp, _dp]),
@@ -148,6 +150,27 @@ def dns_set_velocity_physical(h: int, u) -> None:
 def dns_get_velocity(h: int, out) -> None:
     p, dev, _keep = _buf(out, writable=True)
     _check(load().dns_get_velocity(h, p, dev), "dns_get_velocity")
+
+
+def _host_buf(x, writable: bool = False):
+    p, dev, keep = _buf(x, writable)
+    if dev:
+        raise ValueError("the asynchronous host I/O takes host buffers")
+    return p, keep
+
+
+def dns_set_velocity_async(h: int, uhat) -> None:
+    """Queue the copy of a host field into the state (returns at once; keep
+    uhat alive and unchanged until dns_synchronize)."""
+    p, _keep = _host_buf(uhat)
+    _check(load().dns_set_velocity_async(h, p), "dns_set_velocity_async")
+
+
+def dns_get_velocity_async(h: int, out) -> None:
+    """Queue the read-back of the state into a host buffer (valid after
+    dns_synchronize)."""
+    p, _keep = _host_buf(out, writable=True)
+    _check(load().dns_get_velocity_async(h, p), "dns_get_velocity_async")
 
 
 def dns_rhs(h: int, uhat_in, duhat_out) -> None:
@@ -335,6 +358,7 @@ class Solver:
 
     def __init__(self, N: int, nu: float, dt: float, dtype: int = DNS_F32, stream: int | None = None):
         self.N, self.nu, self.dt, self.dtype = int(N), float(nu), float(dt), int(dtype)
+        self._pending = []  # host buffers of queued asynchronous I/O, held until synchronize()
         self.h = dns_init(N, nu, dt, dtype, stream)
 
     def close(self):
@@ -374,6 +398,20 @@ class Solver:
         dns_get_velocity(self.h, out)
         return out
 
+    def set_velocity_async(self, uhat):
+        """Queue a host field (numpy array or CPU tensor, pinned for overlap)
+        as the next state; it is held until synchronize()."""
+        if isinstance(uhat, np.ndarray):
+            uhat = np.ascontiguousarray(uhat, dtype=io_complex_dtype(self.dtype))
+        dns_set_velocity_async(self.h, uhat)
+        self._pending.append(uhat)
+
+    def get_velocity_async(self, out):
+        """Queue the read-back of the state into a host buffer, valid after
+        synchronize()."""
+        dns_get_velocity_async(self.h, out)
+        self._pending.append(out)
+
     def rhs(self, uhat, out=None):
         if isinstance(uhat, np.ndarray):
             uhat = np.ascontiguousarray(uhat, dtype=io_complex_dtype(self.dtype))
@@ -387,6 +425,7 @@ class Solver:
 
     def synchronize(self):
         dns_synchronize(self.h)
+        self._pending.clear()
 
     def energy(self) -> float:
         return dns_energy(self.h)
