@@ -42,6 +42,18 @@ struct Geo {
     int *err;      // device status word: a bounded wait that gave up writes its code here
 };
 
+// The dealiased geometry is a function of N alone (K = floor((N - 1) / 3), the
+// 2/3 rule); kernels instantiated per mesh size read it as compile-time
+// constants, so their index arithmetic folds and transform stages drop the
+// work on rows known to be zero on input or discarded on output.  Geo carries
+// the same values at run time (dns_init builds it from this formula).
+template <int N> struct GeoN {
+    static constexpr int K = (N - 1) / 3, Kx = 2 * K + 1, Kz = K + 1, Kzp = (Kz + 3) / 4 * 4;
+    static constexpr long long sS = (long long)Kx * Kx * Kzp, sA = (long long)N * Kx * Kzp,
+                               sB = (long long)N * N * Kzp;
+    static constexpr long long bS = 3 * sS, bA = 6 * sA, bB = 6 * sB;
+};
+
 // Arguments of P5b.  stage in 0..3 performs that RK4 stage; stage = -1 writes
 // the right-hand side to dU instead; stage = -2 copies the transform to dU.
 template <typename real, typename acc>
@@ -130,9 +142,9 @@ __global__ void __launch_bounds__(T) k_p1_xinv(Geo g, const typename CT<real>::t
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     const int box = blockIdx.x / 6, f = blockIdx.x % 6, kz0 = blockIdx.y * W, jy = blockIdx.z;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = (f < 3 ? U + f * g.sS : Om + (f - 3) * g.sS) + box * g.bS + (long long)jy * Kzp;
-    cplx *dst = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
+    constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
+    const cplx *src = (f < 3 ? U + f * GeoN<N>::sS : Om + (f - 3) * GeoN<N>::sS) + box * GeoN<N>::bS + (long long)jy * Kzp;
+    cplx *dst = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)jy * Kzp;
     if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, Kx, min(W, Kzp - kz0), &bar);
     load_twiddles<real>(tw, twg, N);
     if constexpr (BULK) {
@@ -199,9 +211,9 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 6, f = blockIdx.z % 6;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
-    cplx *dst = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
+    constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
+    const cplx *src = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)x * Kx * Kzp;
+    cplx *dst = B + box * GeoN<N>::bB + f * GeoN<N>::sB + (long long)x * N * Kzp;
     if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, Kx, min(W, Kzp - kz0), &bar);
     load_twiddles<real>(tw, twg, N);
     if constexpr (BULK) {
@@ -249,9 +261,14 @@ __device__ __forceinline__ void p3_fwd_rest_store(const Geo &g, typename CT<real
                                                   long long line0) {
     typedef typename CT<real>::t cplx;
     constexpr int LDR = row_ld(N);
-    const int K = g.K, Kzp = g.Kzp;
-    const long long sB = g.sB;
-    auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
+    constexpr int K = GeoN<N>::K, Kzp = GeoN<N>::Kzp;
+    constexpr long long sB = GeoN<N>::sB;
+    // the unpack below reads kz <= K of the Nz lines and kz <= K, N - kz of
+    // the others: the last stage stores only those positions (K is a
+    // compile-time constant, so the outputs never read are not computed)
+    auto tstore = [&](int vl, int n, cplx v) {
+        if (n <= K || (vl < L && n >= N - K)) tile[vl * LDR + radd(n)] = v;
+    };
     auto noload = [&](int, int) -> cplx { return cmk<cplx>(0.0, 0.0); };
     constexpr FftPlan P = make_plan(N, MAXR);
     if constexpr (P.nst > 1) RowFFT<real, N, 2 * L, T, -1, MAXR, 1, false, true>::run(tile, tw, noload, tstore);
@@ -406,11 +423,11 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
     load_twiddles<real>(tw, twg, N);
     build_twt<cplx, N, MAXR>(tw + N, twg);
     __syncthreads();
-    const int K = g.K, Kzp = g.Kzp;
+    constexpr int K = GeoN<N>::K, Kzp = GeoN<N>::Kzp;
     const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
     const long long box = lineg / ((long long)N * N), line0 = lineg % ((long long)N * N);
-    const long long sB = g.sB;
-    B += box * g.bB;
+    constexpr long long sB = GeoN<N>::sB;
+    B += box * GeoN<N>::bB;
     // ---- inverse: 3 packed lines per physical line, natural order into the tile
     auto iload = [&](int vl, int n) -> cplx {
         const int p = vl / L, l = vl % L;
@@ -462,11 +479,11 @@ __device__ __forceinline__ void p3_issue(const Geo &g, const typename CT<real>::
                                          uint64_t *bar, long long grp) {
     typedef P3Stage<real, N, L> PS;
     const long long NN = (long long)N * N, lineg = grp * L;
-    const typename CT<real>::t *src = B + (lineg / NN) * g.bB + (lineg % NN) * PS::KZP;
+    const typename CT<real>::t *src = B + (lineg / NN) * GeoN<N>::bB + (lineg % NN) * PS::KZP;
     mbar_arrive_expect_tx(bar, (uint32_t)(6 * PS::field_bytes));
 #pragma unroll
     for (int f = 0; f < 6; ++f)
-        bulk_copy_g2s(stage + f * (L * PS::KZP), src + f * g.sB, (uint32_t)PS::field_bytes, bar);
+        bulk_copy_g2s(stage + f * (L * PS::KZP), src + f * GeoN<N>::sB, (uint32_t)PS::field_bytes, bar);
 }
 
 // One group of L lines from the staging buffer (its copy has landed); issues
@@ -480,7 +497,7 @@ __device__ __noinline__ void p3_tma_group(Geo g, const typename CT<real>::t *tw,
     typedef typename CT<real>::t cplx;
     typedef P3Stage<real, N, L> PS;
     constexpr int LDR = row_ld(N);
-    const int K = g.K;
+    constexpr int K = GeoN<N>::K;
     const long long NN = (long long)N * N;
     const long long lineg = grp * L;
     const long long box = lineg / NN, line0 = lineg % NN;
@@ -500,7 +517,7 @@ __device__ __noinline__ void p3_tma_group(Geo g, const typename CT<real>::t *tw,
     }
     constexpr FftPlan P = make_plan(N, MAXR);
     if constexpr (P.nst > 1) RowFFT<real, N, 3 * L, T, +1, MAXR, 1, false, true>::run(tile, tw, iload, tstore);
-    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * GeoN<N>::bB, line0);
 }
 
 template <typename real, int N, int L, int T, int MAXR>
@@ -573,7 +590,7 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
         return;
     }
     mbar_try_wait(&bar, 0);  // completed: acquire the copied data in every thread
-    const int K = g.K;
+    constexpr int K = GeoN<N>::K;
     const long long NN = (long long)N * N, lineg = grp * L;
     const long long box = lineg / NN, line0 = lineg % NN;
     auto iload = [&](int vl, int n) -> cplx {
@@ -585,7 +602,7 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
-    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+    p3_forward_store<real, N, L, T, MAXR>(g, tile, tw, B + box * GeoN<N>::bB, line0);
 }
 
 // Bulk-fed P3 with the register-fused middle (p3_mid_fused): shared memory
@@ -622,7 +639,7 @@ __device__ __forceinline__ void p3_bulkf_body(Geo g, const typename CT<real>::t 
         return;
     }
     mbar_try_wait(&bar, 0);  // completed: acquire the copied data in every thread
-    const int K = g.K;
+    constexpr int K = GeoN<N>::K;
     const long long NN = (long long)N * N, lineg = grp * L;
     const long long box = lineg / NN, line0 = lineg % NN;
     auto iload = [&](int vl, int n) -> cplx {
@@ -635,7 +652,7 @@ __device__ __forceinline__ void p3_bulkf_body(Geo g, const typename CT<real>::t 
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true, true, true>::run(tile, tw, iload, tstore);
     p3_mid_fused<real, N, L, T, MAXR>(tile, tw);
-    p3_fwd_rest_store<real, N, L, T, MAXR>(g, tile, tw, B + box * g.bB, line0);
+    p3_fwd_rest_store<real, N, L, T, MAXR>(g, tile, tw, B + box * GeoN<N>::bB, line0);
 }
 
 template <typename real, int N, int L, int T, int MAXR>
@@ -684,10 +701,10 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     load_twiddles<real>(tw, twg, N);
-    const int Kz = g.Kz, Kzp = g.Kzp;
+    constexpr int Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const long long line0 = (long long)blockIdx.x * L;  // one box per launch
     const long long N3 = (long long)N * N * N;
-    const long long sB = g.sB;
+    constexpr long long sB = GeoN<N>::sB;
     for (int e = threadIdx.x; e < 2 * L * N; e += T) {
         const int z = e % N, pc = e / N, p = pc / L, c = pc % L;
         const long long off = (line0 + c) * N + z;
@@ -722,9 +739,9 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     const int kz0 = blockIdx.x * W, x = blockIdx.y, box = blockIdx.z / 3, f = blockIdx.z % 3;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = B + box * g.bB + f * g.sB + (long long)x * N * Kzp;
-    cplx *dst = A + box * g.bA + f * g.sA + (long long)x * Kx * Kzp;
+    constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
+    const cplx *src = B + box * GeoN<N>::bB + f * GeoN<N>::sB + (long long)x * N * Kzp;
+    cplx *dst = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)x * Kx * Kzp;
     if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, N, min(W, Kzp - kz0), &bar);
     load_twiddles<real>(tw, twg, N);
     if constexpr (BULK) {
@@ -837,9 +854,9 @@ __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
     const int box = blockIdx.x / 3, f = blockIdx.x % 3, kz0 = blockIdx.y * W, jy = blockIdx.z;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = A + box * g.bA + f * g.sA + (long long)jy * Kzp;
-    cplx *dst = Nh + box * g.bB + f * g.sS + (long long)jy * Kzp;
+    constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
+    const cplx *src = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)jy * Kzp;
+    cplx *dst = Nh + box * GeoN<N>::bB + f * GeoN<N>::sS + (long long)jy * Kzp;
     if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, N, min(W, Kzp - kz0), &bar);
     load_twiddles<real>(tw, twg, N);
     if constexpr (BULK) {
@@ -971,12 +988,12 @@ __global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::
     load_twiddles<real>(tw, twg, N);
     __syncthreads();
     const int box = blockIdx.x, kz0 = blockIdx.y * W, jy = blockIdx.z;
-    const int K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const cplx *src = A + box * g.bA + (long long)jy * Kzp + kz0;
+    constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
+    const cplx *src = A + box * GeoN<N>::bA + (long long)jy * Kzp + kz0;
     auto load = [&](int n, int c) -> cplx {
         const int f = c / W, cc = c % W;
         if (kz0 + cc >= Kz) return cmk<cplx>(0.0, 0.0);
-        return src[f * g.sA + (long long)n * Kx * Kzp + cc];
+        return src[f * GeoN<N>::sA + (long long)n * Kx * Kzp + cc];
     };
     auto tstore = [&](int n, int c, cplx v) { tile[n * WT + c] = v; };
     TileFFT<real, N, WT, T, -1, MAXR>::run(tile, WT, tw, load, tstore);
