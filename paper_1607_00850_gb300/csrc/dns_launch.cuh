@@ -250,10 +250,16 @@ template <typename real, typename acc> struct UpdLaunch {
         a.ifrk = e.ifrk;
         return a;
     }
+};
+
+// The update pass of one mesh size (its index arithmetic uses N's geometry).
+template <typename real, typename acc, int N> struct UpdLaunchN {
+    typedef typename CT<real>::t cplx;
     static cudaError_t p5b(const Geo &g, const void *Nh, const UpdateArgsErased &e, cudaStream_t st) {
-        const long long n = g.sS * g.nb;
-        const unsigned blocks = (unsigned)((n + 255) / 256);
-        k_p5b_update<real, acc><<<blocks, 256, 0, st>>>(g, (const cplx *)Nh, args(e));
+        static_assert(GeoN<N>::sS < (1ll << 31), "one field's stored modes index with int");
+        if (g.nb < 1 || g.nb > 65535) return cudaErrorInvalidValue;
+        const dim3 grid((unsigned)((GeoN<N>::sS + 255) / 256), (unsigned)g.nb);
+        k_p5b_update<real, acc, N><<<grid, 256, 0, st>>>((const cplx *)Nh, UpdLaunch<real, acc>::args(e));
         return cudaGetLastError();
     }
 };
@@ -346,7 +352,7 @@ template <int N> bool fill_passes(int dtype, PassSet *ps) {
         fill_col<double, N, 0>(ps);
         fill_p3<double, N, 0>(ps);
         ps->curl = MiscLaunch<double, N>::curl;
-        ps->p5b = UpdLaunch<double, double>::p5b;
+        ps->p5b = UpdLaunchN<double, double, N>::p5b;
         fill_p5f<double, double, N, 0>(ps);
         ps->zfwd = MiscLaunch<double, N>::template zfwd<double>;
         ps->prep_misc = MiscLaunch<double, N>::template prepare<double>;
@@ -357,12 +363,12 @@ template <int N> bool fill_passes(int dtype, PassSet *ps) {
         fill_p3<float, N, 0>(ps);
         ps->curl = MiscLaunch<float, N>::curl;
         if (dtype == 0) {
-            ps->p5b = UpdLaunch<float, float>::p5b;
+            ps->p5b = UpdLaunchN<float, float, N>::p5b;
             fill_p5f<float, float, N, 0>(ps);
             ps->zfwd = MiscLaunch<float, N>::template zfwd<float>;
             ps->prep_misc = MiscLaunch<float, N>::template prepare<float>;
         } else {
-            ps->p5b = UpdLaunch<float, double>::p5b;
+            ps->p5b = UpdLaunchN<float, double, N>::p5b;
             fill_p5f<float, double, N, 0>(ps);
             ps->zfwd = MiscLaunch<float, N>::template zfwd<double>;
             ps->prep_misc = MiscLaunch<float, N>::template prepare<double>;

@@ -883,14 +883,15 @@ __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::
 // term n0..n2: optional forcing, Leray projection (Eq. pressure / NSfinal),
 // viscous term and the RK4 (or IF-RK4) stage, then omega^ of the next stage
 // input for the next P1.
-template <typename real, typename acc>
-__device__ __forceinline__ void p5_mode_update(const Geo &g, const UpdateArgs<real, acc> &args, long long box, int ix,
-                                               int iy, int kz, typename CT<real>::t n0, typename CT<real>::t n1,
+template <typename real, typename acc, int N>
+__device__ __forceinline__ void p5_mode_update(const UpdateArgs<real, acc> &args, int box, int ix, int iy, int kz,
+                                               typename CT<real>::t n0, typename CT<real>::t n1,
                                                typename CT<real>::t n2) {
     typedef typename CT<real>::t cplx;
     typedef typename CT<acc>::t cacc;
-    const long long sS = g.sS;
-    const long long m = box * g.bS + ((long long)ix * g.Kx + iy) * g.Kzp + kz;  // state element, component 0
+    typedef GeoN<N> G;
+    constexpr long long sS = G::sS;
+    const long long m = box * G::bS + ((long long)ix * G::Kx + iy) * G::Kzp + kz;  // state element, component 0
     const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
     if (args.Fext && args.stage != -2) {
         const cplx f0 = args.Fext[m], f1 = args.Fext[sS + m], f2 = args.Fext[2 * sS + m];
@@ -917,7 +918,7 @@ __device__ __forceinline__ void p5_mode_update(const Geo &g, const UpdateArgs<re
         if (args.stage >= 0 && args.stage < 3) s0[c] = args.U0[c * sS + m];
         if (args.stage > 0) s1[c] = args.U1[c * sS + m];
     }
-    const real kx = (real)compact_to_k(ix, g.K), ky = (real)compact_to_k(iy, g.K), kzr = (real)kz;
+    const real kx = (real)compact_to_k(ix, G::K), ky = (real)compact_to_k(iy, G::K), kzr = (real)kz;
     const real k2 = kx * kx + ky * ky + kzr * kzr;
     const real inv = k2 > 0 ? (real)1 / k2 : (real)0;
     const real dre = (kx * n0.x + ky * n1.x + kzr * n2.x) * inv;
@@ -953,23 +954,22 @@ __device__ __forceinline__ void p5_mode_update(const Geo &g, const UpdateArgs<re
     }
 }
 
-template <typename real, typename acc>
-__global__ void k_p5b_update(Geo g, const typename CT<real>::t *__restrict__ Nh, UpdateArgs<real, acc> args) {
+// Grid: (stored modes of one field / blockDim.x, boxes); one mode per thread
+// (no grid-stride loop: every thread's loads are independent, which keeps
+// enough bytes in flight), its indices by divisions by compile-time constants.
+template <typename real, typename acc, int N>
+__global__ void k_p5b_update(const typename CT<real>::t *__restrict__ Nh, UpdateArgs<real, acc> args) {
     typedef typename CT<real>::t cplx;
-    const int Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const long long sS = g.sS;
-    // one mode per thread (no grid-stride loop): every thread's loads are
-    // independent, which keeps enough bytes in flight
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= sS * g.nb) return;
-    const long long box = e / sS, mm = e % sS;
-    const int kz = (int)(mm % Kzp);
-    if (kz >= Kz) return;
-    const long long r = mm / Kzp;
-    const int iy = (int)(r % Kx), ix = (int)(r / Kx);
-    const long long nm = box * g.bB + mm;  // N^ lives in B, state layout
-    const cplx n0 = Nh[nm], n1 = Nh[sS + nm], n2 = Nh[2 * sS + nm];
-    p5_mode_update<real, acc>(g, args, box, ix, iy, kz, n0, n1, n2);
+    typedef GeoN<N> G;
+    const int mm = blockIdx.x * blockDim.x + threadIdx.x, box = blockIdx.y;
+    if (mm >= G::sS) return;
+    const int kz = mm % G::Kzp;
+    if (kz >= G::Kz) return;
+    const int r = mm / G::Kzp;
+    const int iy = r % G::Kx, ix = r / G::Kx;
+    const long long nm = box * G::bB + mm;  // N^ lives in B, state layout
+    const cplx n0 = Nh[nm], n1 = Nh[G::sS + nm], n2 = Nh[2 * G::sS + nm];
+    p5_mode_update<real, acc, N>(args, box, ix, iy, kz, n0, n1, n2);
 }
 
 // P5a and P5b in one pass: a block transforms all three fields of one
@@ -1003,7 +1003,7 @@ __global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::
         const int kx = compact_to_k(ix, K);
         const int n = kx >= 0 ? kx : kx + N;
         const cplx *row = tile + n * WT + cc;
-        p5_mode_update<real, acc>(g, args, box, ix, jy, kz, row[0], row[W], row[2 * W]);
+        p5_mode_update<real, acc, N>(args, box, ix, jy, kz, row[0], row[W], row[2 * W]);
     }
 }
 
