@@ -118,16 +118,23 @@ static inline int grid_for(long long total) {
 }
 
 // --------------------------------------------------------------- conversions
-template <typename Tin, typename Tout>
-static cudaError_t to_compact(const dns_ctx *h, const void *full, void *cmp) {
-    const long long total = 3LL * h->g.Kx * h->g.Kx * h->g.Kz;
-    dns::k_full_to_compact<Tin, Tout><<<grid_for(total), 256, 0, h->stream>>>(h->g, (const Tin *)full, (Tout *)cmp);
+static inline unsigned row_threads(int n) {
+    const int t = (n + 31) / 32 * 32;
+    return (unsigned)(t < 1024 ? t : 1024);
+}
+// full -> compact (cmp2: a second compact copy, or nullptr)
+template <typename Tin, typename Tout, typename Tout2>
+static cudaError_t to_compact(const dns_ctx *h, const void *full, void *cmp, void *cmp2) {
+    const dim3 grid((unsigned)h->g.Kx, (unsigned)h->g.Kx, 3);
+    dns::k_full_to_compact<Tin, Tout, Tout2><<<grid, row_threads(h->g.Kz), 0, h->stream>>>(
+        h->g, (const Tin *)full, (Tout *)cmp, (Tout2 *)cmp2);
     return cudaGetLastError();
 }
 template <typename Tin, typename Tout>
 static cudaError_t to_full(const dns_ctx *h, const void *cmp, void *full) {
-    const long long total = 3LL * h->N * h->N * (h->N / 2 + 1);
-    dns::k_compact_to_full<Tin, Tout><<<grid_for(total), 256, 0, h->stream>>>(h->g, (const Tin *)cmp, (Tout *)full);
+    const dim3 grid((unsigned)h->N, (unsigned)h->N, 3);
+    dns::k_compact_to_full<Tin, Tout><<<grid, row_threads(h->N / 2 + 1), 0, h->stream>>>(h->g, (const Tin *)cmp,
+                                                                                         (Tout *)full);
     return cudaGetLastError();
 }
 
@@ -144,18 +151,10 @@ __global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ b, long 
 
 // full (io type) -> compact (real type) and compact (acc type)
 static cudaError_t full_to_state(dns_ctx *h, const void *full, void *dst_real, void *dst_acc) {
-    cudaError_t e = cudaSuccess;
-    if (h->dtype == DNS_F32) {
-        if (dst_real) e = to_compact<float2, float2>(h, full, dst_real);
-        if (e == cudaSuccess && dst_acc) e = to_compact<float2, float2>(h, full, dst_acc);
-    } else if (h->dtype == DNS_F64) {
-        if (dst_real) e = to_compact<double2, double2>(h, full, dst_real);
-        if (e == cudaSuccess && dst_acc) e = to_compact<double2, double2>(h, full, dst_acc);
-    } else {
-        if (dst_real) e = to_compact<double2, float2>(h, full, dst_real);
-        if (e == cudaSuccess && dst_acc) e = to_compact<double2, double2>(h, full, dst_acc);
-    }
-    return e;
+    // one pass over the input writes both copies (dst_real is never nullptr)
+    if (h->dtype == DNS_F32) return to_compact<float2, float2, float2>(h, full, dst_real, dst_acc);
+    if (h->dtype == DNS_F64) return to_compact<double2, double2, double2>(h, full, dst_real, dst_acc);
+    return to_compact<double2, float2, double2>(h, full, dst_real, dst_acc);
 }
 
 // compact (acc type) -> full (io type); io type == acc type in every mode

@@ -1009,45 +1009,53 @@ __global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::
 
 // ------------------------------------------------------------------- layout conversion
 // full [3][N][N][N/2+1] <-> compact state layout; modes outside the kept set
-// are dropped on the way in and zero on the way out.
-template <typename Tin, typename Tout>
-__global__ void k_full_to_compact(Geo g, const Tin *__restrict__ full, Tout *__restrict__ cmp) {
+// are dropped on the way in and zero on the way out.  One block per row:
+// grid (y, x, component), the threads along kz (contiguous on both sides),
+// so no index is divided.
+
+// Kept rows in, to one or two compact buffers (cmp2 may be nullptr).
+template <typename Tin, typename Tout, typename Tout2>
+__global__ void k_full_to_compact(Geo g, const Tin *__restrict__ full, Tout *__restrict__ cmp,
+                                  Tout2 *__restrict__ cmp2) {
     const int N = g.N, Nh = N / 2 + 1, K = g.K, Kx = g.Kx, Kz = g.Kz, Kzp = g.Kzp;
-    const long long total = 3LL * Kx * Kx * Kz;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(e % Kz);
-        const long long r = e / Kz;
-        const int iy = (int)(r % Kx), ix = (int)((r / Kx) % Kx), c = (int)(r / ((long long)Kx * Kx));
-        const int fx = ix <= K ? ix : ix - Kx + N, fy = iy <= K ? iy : iy - Kx + N;
-        const Tin v = full[(((long long)c * N + fx) * N + fy) * Nh + kz];
-        Tout o;
-        o.x = v.x;
-        o.y = v.y;
-        cmp[c * g.sS + ((long long)ix * Kx + iy) * Kzp + kz] = o;
+    const int iy = blockIdx.x, ix = blockIdx.y, c = blockIdx.z;
+    const int fx = ix <= K ? ix : ix - Kx + N, fy = iy <= K ? iy : iy - Kx + N;
+    const Tin *src = full + (((long long)c * N + fx) * N + fy) * Nh;
+    const long long o = c * g.sS + ((long long)ix * Kx + iy) * Kzp;
+    for (int kz = threadIdx.x; kz < Kz; kz += blockDim.x) {
+        const Tin v = src[kz];
+        Tout a;
+        a.x = v.x;
+        a.y = v.y;
+        cmp[o + kz] = a;
+        if (cmp2) {
+            Tout2 b;
+            b.x = v.x;
+            b.y = v.y;
+            cmp2[o + kz] = b;
+        }
     }
 }
 
 template <typename Tin, typename Tout>
 __global__ void k_compact_to_full(Geo g, const Tin *__restrict__ cmp, Tout *__restrict__ full) {
     const int N = g.N, Nh = N / 2 + 1, K = g.K, Kx = g.Kx, Kzp = g.Kzp;
-    const long long total = 3LL * N * N * Nh;
-    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
-         e += (long long)gridDim.x * blockDim.x) {
-        const int kz = (int)(e % Nh);
-        const long long r = e / Nh;
-        const int fy = (int)(r % N), fx = (int)((r / N) % N), c = (int)(r / ((long long)N * N));
-        const int ix = fx <= K ? fx : (fx >= N - K ? fx - N + Kx : -1);
-        const int iy = fy <= K ? fy : (fy >= N - K ? fy - N + Kx : -1);
+    const int fy = blockIdx.x, fx = blockIdx.y, c = blockIdx.z;
+    const int ix = fx <= K ? fx : (fx >= N - K ? fx - N + Kx : -1);
+    const int iy = fy <= K ? fy : (fy >= N - K ? fy - N + Kx : -1);
+    Tout *dst = full + (((long long)c * N + fx) * N + fy) * Nh;
+    const bool kept = ix >= 0 && iy >= 0;
+    const Tin *src = cmp + c * g.sS + (kept ? ((long long)ix * Kx + iy) * Kzp : 0);
+    for (int kz = threadIdx.x; kz < Nh; kz += blockDim.x) {
         Tout o;
         o.x = 0;
         o.y = 0;
-        if (ix >= 0 && iy >= 0 && kz <= K) {
-            const Tin v = cmp[c * g.sS + ((long long)ix * Kx + iy) * Kzp + kz];
+        if (kept && kz <= K) {
+            const Tin v = src[kz];
             o.x = v.x;
             o.y = v.y;
         }
-        full[e] = o;
+        dst[kz] = o;
     }
 }
 
