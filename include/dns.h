@@ -292,6 +292,15 @@ int dns_les_set_closure(dns_handle h, dns_net net);
  * dns_les_set_closure(h, NULL).  Same handle restrictions as above;
  * DNS_ERR_ARG for cs < 0 or non-finite arguments. */
 int dns_les_set_smagorinsky(dns_handle h, double cs, double delta);
+/* When the closure term of an attached closure is evaluated: every_stage = 1
+ * (default) from each RK4 stage's input; 0 from the first stage's input (the
+ * state at the start of the step) only, the same term then held through the
+ * step's four stages (one network evaluation per step instead of four; the
+ * closure term becomes first-order accurate in time, the resolved dynamics
+ * stay RK4).  Takes effect at the next dns_step (the step graph is
+ * re-captured); dns_rhs always evaluates it from its input.  DNS_ERR_ARG for
+ * other values. */
+int dns_les_set_closure_stages(dns_handle h, int every_stage);
 
 /* ------------------------------------------------------------------------
  * Diagnostics without allocation.  The paper has no counterpart: this is a

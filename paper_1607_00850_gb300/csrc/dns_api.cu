@@ -59,6 +59,7 @@ struct dns_ctx {
     int integrator = 0;             // DNS_RK4 or DNS_IFRK4
     dns::LesClosure *closure = nullptr;  // learned subgrid closure (LES handles), or nullptr
     void *Fext = nullptr;                // its forcing on the stored modes
+    int closure_every_stage = 1;         // 0: evaluated from the step's first stage input only
     // asynchronous host I/O (created on first use): a copy-in and a copy-out
     // stream, one staging buffer in and two out (full spectral layout)
     cudaStream_t s_in = nullptr, s_out = nullptr;
@@ -224,7 +225,7 @@ static cudaError_t enqueue_step(dns_ctx *h, cudaEvent_t *ev) {
     const double scale = 1.0 / ((double)h->N * h->N * h->N);
     for (int s = 0; s < 4; ++s) {
         dns::UpdateArgsErased a = stage_args(h, s);
-        if (h->closure) {  // subgrid forcing from this stage's input
+        if (h->closure && (s == 0 || h->closure_every_stage)) {  // subgrid forcing from this stage's input
             if ((e = dns::les_closure_forcing(h->closure, h->g, a.U, h->Fext, h->stream)) != cudaSuccess) return e;
         }
         if ((e = h->ps.p1[h->plan[0]](h->g, h->tw, a.U, h->Om, h->A, scale, h->stream)) != cudaSuccess) return e;
@@ -918,6 +919,15 @@ int dns_set_integrator(dns_handle h, int kind) {
     if (kind != h->integrator) {
         h->integrator = kind;
         drop_graph(h);
+    }
+    return DNS_OK;
+}
+
+int dns_les_set_closure_stages(dns_handle h, int every_stage) {
+    if (!h || (every_stage != 0 && every_stage != 1)) return DNS_ERR_ARG;
+    if (h->closure_every_stage != every_stage) {
+        h->closure_every_stage = every_stage;
+        drop_graph(h);  // the captured step holds the old choice
     }
     return DNS_OK;
 }

@@ -75,6 +75,7 @@ SIGNATURES = {
     "dns_les_builder_run": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "dns_les_set_closure": (_i, [_vp, _vp]),
     "dns_les_set_smagorinsky": (_i, [_vp, _d, _d]),
+    "dns_les_set_closure_stages": (_i, [_vp, _i]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -582,6 +583,11 @@ def dns_les_set_closure(h: int, net: int | None) -> None:
 def dns_les_set_smagorinsky(h: int, cs: float, delta: float = 0.0) -> None:
     """Smagorinsky closure tau = -2 (cs delta)^2 |S| S; delta <= 0: mesh spacing."""
     _check(load().dns_les_set_smagorinsky(h, float(cs), float(delta)), "dns_les_set_smagorinsky")
+
+
+def dns_les_set_closure_stages(h: int, every_stage: bool) -> None:
+    """Evaluate an attached closure at every RK4 stage (True) or once per step."""
+    _check(load().dns_les_set_closure_stages(h, 1 if every_stage else 0), "dns_les_set_closure_stages")
 
 
 def dns_net_set_closure_scaling(net: int, in_scale: float, out_scale: float) -> None:

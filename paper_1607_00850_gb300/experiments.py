@@ -108,7 +108,9 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
        passes; the loss on a held-out seed is reported per epoch.
     3. A posteriori: from the filtered field of a held-out seed, `eval_steps`
        LES steps without a model, with Smagorinsky (C_s = cs, Delta = mesh
-       spacing) and with the learned closure, against the filtered DNS;
+       spacing), with the learned closure evaluated at every RK4 stage and
+       with it evaluated once per step (held through the stages), against
+       the filtered DNS;
        resolved energy and the log-spectrum error over k <= kc every
        `eval_every` steps."""
     import torch
@@ -189,50 +191,57 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
         ub = torch.empty((3, n, n, n // 2 + 1), dtype=torch.complex64, device=dev)
         g1 = torch.empty((9, n, n, n), device=dev)
         t1 = torch.empty((6, n, n, n), device=dev)
-        models = ("no_model", "smagorinsky", "learned")
+        # learned_once: the same closure evaluated once per step (at the step's
+        # first stage) and held through its four stages
+        models = ("no_model", "smagorinsky", "learned", "learned_once")
         hist = {m: [] for m in models + ("filtered_dns",)}
         with dns.Solver(N, nu, dt, dns.DNS_F32) as d, dns.Solver(n, nu, dt, dns.DNS_F32) as ref, \
                 dns.Solver(n, nu, dt, dns.DNS_F32) as a, dns.Solver(n, nu, dt, dns.DNS_F32) as sm, \
-                dns.Solver(n, nu, dt, dns.DNS_F32) as le:
+                dns.Solver(n, nu, dt, dns.DNS_F32) as le, dns.Solver(n, nu, dt, dns.DNS_F32) as lo:
+            les = (a, sm, le, lo)
             b = dns.dns_les_builder_create(N, n)
             try:
                 d.set_velocity(inputs.random_isotropic(N, seed=seed0 + seeds + 1, k0=k0))
                 d.step(spinup)
                 dns.dns_les_builder_run(b, d.h, g1, t1, ub)
-                for s in (a, sm, le):
+                for s in les:
                     s.set_velocity(ub)
                 dns.dns_les_set_smagorinsky(sm.h, cs)
                 dns.dns_les_set_closure(le.h, net)
+                dns.dns_les_set_closure(lo.h, net)
+                dns.dns_les_set_closure_stages(lo.h, False)
                 done = 0
                 while True:
                     dns.dns_les_builder_run(b, d.h, g1, t1, ub)
                     ref.set_velocity(ub)
                     eref = ref.spectrum()
                     hist["filtered_dns"].append({"step": done, "E": ref.energy()})
-                    for m, s in zip(models, (a, sm, le)):
+                    for m, s in zip(models, les):
                         e = s.spectrum()
                         mx, mean = _shell_errors(e, eref, kc)
                         hist[m].append({"step": done, "E": s.energy(),
                                         "log_spectrum_err": _log_spectrum_error(e, eref, kc),
                                         "shell_rel_err_max": mx, "shell_rel_err_mean": mean})
                     if done >= eval_steps:
-                        final = {m: s.spectrum()[:kc + 2].tolist() for m, s in zip(models, (a, sm, le))}
+                        final = {m: s.spectrum()[:kc + 2].tolist() for m, s in zip(models, les)}
                         final["filtered_dns"] = eref[:kc + 2].tolist()
                         break
                     k = min(eval_every, eval_steps - done)
-                    for s in (d, a, sm, le):
+                    for s in (d,) + les:
                         s.step(k)
                     done += k
                 dns.dns_les_set_closure(le.h, None)
+                dns.dns_les_set_closure(lo.h, None)
             finally:
                 dns.dns_les_builder_free(b)
         # cost of one LES step with and without the learned closure
         with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
             s.set_velocity(ub)
             cost = {}
-            for name in ("no_model", "learned", "smagorinsky"):
-                if name == "learned":
+            for name in ("no_model", "learned", "learned_once", "smagorinsky"):
+                if name in ("learned", "learned_once"):
                     dns.dns_les_set_closure(s.h, net)
+                    dns.dns_les_set_closure_stages(s.h, name == "learned")
                 elif name == "smagorinsky":
                     dns.dns_les_set_smagorinsky(s.h, cs)
                 s.step(3)
@@ -242,6 +251,7 @@ def les_closure(N: int = 256, n: int = 64, nu: float = 1e-3, dt: float = 0.002, 
                 s.synchronize()
                 cost[name + "_ms_per_step"] = (time.perf_counter() - tt) / 20 * 1e3
                 dns.dns_les_set_closure(s.h, None)
+                dns.dns_les_set_closure_stages(s.h, True)
         with dns.Solver(N, nu, dt, dns.DNS_F32) as s:
             s.set_velocity(inputs.random_isotropic(N, seed=1, k0=k0))
             s.step(3)
@@ -311,9 +321,10 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
         out["train_ms_per_sample"] = (time.perf_counter() - t0) / (k * batch) * 1e3
         with dns.Solver(n, 1e-3, 2e-3, dns.DNS_F32) as s:
             s.set_velocity(inputs.random_isotropic(n, seed=3))
-            for mode in ("no_model", "smagorinsky", "learned"):
-                if mode == "learned":
+            for mode in ("no_model", "smagorinsky", "learned", "learned_once"):
+                if mode in ("learned", "learned_once"):
                     dns.dns_les_set_closure(s.h, net)
+                    dns.dns_les_set_closure_stages(s.h, mode == "learned")
                 elif mode == "smagorinsky":
                     dns.dns_les_set_smagorinsky(s.h, 0.17)
                 s.step(3)
@@ -323,6 +334,7 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
                 s.synchronize()
                 out[f"les_step_ms_{mode}"] = (time.perf_counter() - t0) / reps * 1e3
                 dns.dns_les_set_closure(s.h, None)
+                dns.dns_les_set_closure_stages(s.h, True)
         with dns.Solver(dns_N, 1e-3, 2e-3, dns.DNS_F32) as s:
             s.set_velocity(inputs.random_isotropic(dns_N, seed=3))
             s.step(3)

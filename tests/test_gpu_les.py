@@ -211,6 +211,45 @@ def test_smagorinsky_closure_matches_oracle(dns, orc):
     assert rel(got.astype(np.complex128) - base, ref) < 1e-4
 
 
+def test_closure_once_per_step_matches_oracle(dns, orc):
+    # closure term evaluated from the step-start state only and held through
+    # the four RK4 stages: u1 = RK4 of du/dt = RHS(u) + F0 with F0 the closure
+    # term of u0 (built from the oracle's right-hand sides)
+    n, nu, dt, cs = 16, 0.01, 0.05, 0.17
+    ub = inputs.random_isotropic(n, seed=78, k0=3.0).astype(np.complex64)
+    with dns.Solver(n, nu, dt, dns.DNS_F32) as s:
+        dns.dns_les_set_smagorinsky(s.h, cs)
+        dns.dns_les_set_closure_stages(s.h, False)
+        s.set_velocity(ub)
+        s.step(1)
+        once = s.get_velocity()
+        dns.dns_les_set_closure_stages(s.h, True)
+        s.set_velocity(ub)
+        s.step(1)
+        every = s.get_velocity()
+        assert dns.STATUS[dns.load().dns_les_set_closure_stages(s.h, 2)] == "DNS_ERR_ARG"
+    u0 = ub.astype(np.complex128)
+
+    def closure_term(u):
+        _, g, _ = orc.les_inputs(u, n)
+        return orc.rhs_les(u, nu, orc.smagorinsky(g, cs, 2 * np.pi / n)) - orc.rhs(u, nu)
+
+    def rk4(f):
+        k1 = f(u0, 0)
+        k2 = f(u0 + 0.5 * dt * k1, 1)
+        k3 = f(u0 + 0.5 * dt * k2, 2)
+        k4 = f(u0 + dt * k3, 3)
+        return u0 + dt / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+    f0 = closure_term(u0)
+    ref_once = rk4(lambda u, i: orc.rhs(u, nu) + f0)
+    ref_every = rk4(lambda u, i: orc.rhs(u, nu) + closure_term(u))
+    assert rel(once, ref_once) < 1e-5
+    assert rel(every, ref_every) < 1e-5
+    # the two schedules differ by more than the rounding
+    assert rel(ref_once, ref_every) > 5 * max(rel(once, ref_once), rel(every, ref_every))
+
+
 def test_smagorinsky_dissipates(dns):
     n, nu, dt = 32, 0.002, 0.005
     u0 = inputs.random_isotropic(n, seed=77, k0=4.0)
