@@ -148,6 +148,14 @@ int dns_set_integrator(dns_handle h, int kind);
  * state is then not trustworthy and the status stays set). */
 int dns_synchronize(dns_handle h);
 
+/* Check of the failure detection above: queue on the handle's stream a
+ * one-block kernel whose bounded wait (on an mbarrier nothing completes)
+ * gives up after `seconds` (0 < seconds <= 2, else DNS_ERR_ARG), so that the
+ * next dns_synchronize returns DNS_ERR_TIMEOUT.  Leaves the handle's status
+ * set, as a real timeout does; the CUDA context stays usable.  For tests of
+ * the error path; faults nothing. */
+int dns_check_wait_timeout(dns_handle h, double seconds);
+
 /* Diagnostics of the current state, accumulated in double (synchronising):
  * E = <|u|^2>/2, eps = nu <|grad u|^2>, and the shell spectrum
  * Ek[s] = sum over modes with floor(|k| + 1/2) = s of |uhat|^2 / (2 N^6)

@@ -462,6 +462,26 @@ int dns_synchronize(dns_handle h) {
 
 }  // extern "C"
 
+// The device side of the failure detection, exercised on purpose: one thread
+// arms an mbarrier that nothing will ever complete and waits on it with the
+// same bounded wait the bulk-copy consumers use, for limit_ns; the wait gives
+// up, the code goes to the handle's status word and the kernel returns.  No
+// copy is in flight, so nothing is left behind.
+__global__ void k_wait_timeout_check(int *err, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        dns::mbar_init(&bar, 1);
+        if (!dns::mbar_wait_bounded(&bar, 0, limit_ns)) dns::record_error(err, dns::kErrWaitTimeout);
+    }
+}
+
+extern "C" int dns_check_wait_timeout(dns_handle h, double seconds) {
+    if (!h || !(seconds > 0.0) || !(seconds <= 2.0)) return DNS_ERR_ARG;
+    k_wait_timeout_check<<<1, 32, 0, h->stream>>>(h->err, (unsigned long long)(seconds * 1e9));
+    CK(cudaGetLastError());
+    return DNS_OK;
+}
+
 // Streams, events and staging buffers of the asynchronous host I/O, made on
 // first use; a failure leaves none of them behind.
 static void drop_async_io(dns_ctx *h) {

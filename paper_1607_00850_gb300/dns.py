@@ -37,6 +37,7 @@ SIGNATURES = {
     "dns_step": (_i, [_vp, _i]),
     "dns_step_profiled": (_i, [_vp, _i, _dp, _dp]),
     "dns_synchronize": (_i, [_vp]),
+    "dns_check_wait_timeout": (_i, [_vp, _d]),
     "dns_energy": (_i, [_vp, _dp]),
     "dns_dissipation": (_i, [_vp, _dp]),
     "dns_spectrum": (_i, [_vp, _dp, _i]),
@@ -196,6 +197,12 @@ def dns_step_profiled(h: int, n: int):
 
 def dns_synchronize(h: int) -> None:
     _check(load().dns_synchronize(h), "dns_synchronize")
+
+
+def dns_check_wait_timeout(h: int, seconds: float) -> None:
+    """Queue a kernel whose bounded device wait gives up after `seconds`
+    (the next dns_synchronize reports DNS_ERR_TIMEOUT)."""
+    _check(load().dns_check_wait_timeout(h, float(seconds)), "dns_check_wait_timeout")
 
 
 def dns_energy(h: int) -> float:

@@ -385,6 +385,33 @@ def test_nonfinite_state_is_reported(dns):
         assert e.value.status == 5
 
 
+def test_bounded_wait_timeout_is_reported_and_context_survives(dns):
+    # failure detection without a fault: a kernel's bounded wait on an
+    # mbarrier that nothing completes gives up after 20 ms, writes its code to
+    # the handle's status word and returns; the next synchronize reports it
+    import time
+    u = inputs.random_isotropic(16, seed=5).astype(np.complex64)
+    with dns.Solver(16, 0.01, 0.01, dns.DNS_F32) as s:
+        s.set_velocity(u)
+        s.synchronize()
+        t0 = time.perf_counter()
+        dns.dns_check_wait_timeout(s.h, 0.02)
+        with pytest.raises(dns.DnsError) as ex:
+            s.synchronize()
+        assert ex.value.status == 4 and "DNS_ERR_TIMEOUT" in str(ex.value)
+        assert time.perf_counter() - t0 < 5.0
+        with pytest.raises(dns.DnsError) as ex:
+            dns.dns_check_wait_timeout(s.h, 0.0)
+        assert ex.value.status == 1
+    # the CUDA context is intact: a new handle runs and decays as it should
+    with dns.Solver(16, 0.01, 0.01, dns.DNS_F32) as s:
+        s.set_velocity(u)
+        e0 = s.energy()
+        s.step(2)
+        s.synchronize()
+        assert s.energy() < e0
+
+
 def test_bad_arguments_on_live_handle(dns):
     with dns.Solver(16, 0.01, 0.01, dns.DNS_F32) as s:
         lib = dns.load()
