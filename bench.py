@@ -206,6 +206,16 @@ def unpruned_step_bytes(N, dtype):
     return 216 * N * N * (N // 2 + 1) * cr
 
 
+FUSED_P5_FROM = 8  # plan[4] values from here on select a fused x-forward + update variant
+
+
+def step_launches(plan) -> int:
+    """Kernel launches of one RK4 step (the graph a timed step replays): six
+    passes per stage, five when the x-forward transform and the update are
+    fused."""
+    return 4 * (5 if plan[4] >= FUSED_P5_FROM else 6)
+
+
 def max_over_ranks(x: float, dist=None, device: str = "cuda") -> float:
     """The largest x over all ranks (the job's time is its slowest rank's)."""
     if dist is None:
@@ -382,7 +392,7 @@ def run_ours(args, rank, world, local_rank):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded random-phase isotropic field)", "config": cfg,
             "parallelism": "replicas" if world > 1 else "single GPU",
-            "gpu_launches": 24 * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
+            "gpu_launches": step_launches(plan) * args.steps, "roofline": roofline, "clocks": clk, "e2e": e2e,
             "cpu_baseline": cpu, "energy": {"initial": E0, "after_steps": E32},
             "plan": {"variants": plan, "shapes (lines, radix cap, threads)": shapes}, **extra}
     return line

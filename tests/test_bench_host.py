@@ -112,3 +112,9 @@ def test_whole_job_rate_counts_every_replica():
 def test_step_flops_grow_as_n3_log_n():
     r = bench.step_flops(1024) / bench.step_flops(512)
     assert 8.0 < r < 8.0 * (10 / 9) * 1.05
+
+
+def test_step_launch_count_follows_the_plan():
+    assert bench.step_launches([7, 7, 9, 3, 0]) == 24
+    assert bench.step_launches([7, 7, 9, 3, 7]) == 24
+    assert bench.step_launches([7, 7, 9, 3, bench.FUSED_P5_FROM]) == 20
