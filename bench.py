@@ -479,6 +479,11 @@ def run_reference(args, rank, world):
     uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
     dt = inputs.cfl_dt(uh, 0.5)
     o.rhs(inputs.random_isotropic(32, seed=1), 1e-3)   # warm the code once, small
+    # W untimed warm-up steps of the workload itself (bounded to a minute)
+    warm, tw = 0, time.perf_counter()
+    while warm < max(0, args.warmup) and time.perf_counter() - tw < 60.0:
+        o.rhs(uh, 1.0 / 4000.0)
+        warm += 1
     budget = 150.0
     t0 = time.perf_counter()
     n = 0
@@ -492,7 +497,7 @@ def run_reference(args, rank, world):
     cores = o.num_threads()
     sample = f"{n} right-hand sides at {N}^3 (each 1/4 RK4 step), {t:.1f} s"
     return {"metric": METRIC, "value": value, "unit": "grid-point-steps/s", "n_gpus": world, "steps": n,
-            "warmup": 1, "ms_per_step": 4 * t / n * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": warm, "ms_per_step": 4 * t / n * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded random-phase isotropic field)",
             "config": config(N, dt), "impl": "reference",
             "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": sample, "value": value,
