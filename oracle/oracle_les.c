@@ -16,8 +16,15 @@
  * (xx, yy, zz, xy, xz, yz) out; loss = mean of squared errors.
  *
  * Layouts: channel-major [C][n][n][n] (z fastest); weights [Cout][Cin][27].
+ *
+ * OR_MUTANT 8..13 plant one deliberate mistake each in this file (see
+ * oracle.c); the LES pins must reject every one.
  */
 #include "oracle.h"
+
+#ifndef OR_MUTANT
+#define OR_MUTANT 0
+#endif
 
 #include <complex.h>
 #include <math.h>
@@ -46,7 +53,11 @@ int or_conv3d_fwd(int n, int cin, int cout, const double *x, const double *w, co
                     double s = b ? b[o] : 0.0;
                     for (int c = 0; c < cin; ++c)
                         for (int t = 0; t < 27; ++t) {
+#if OR_MUTANT == 8 /* planted: convolution (flipped taps) instead of cross-correlation */
+                            const int tx = 1 - t / 9, ty = 1 - (t / 3) % 3, tz = 1 - t % 3;
+#else
                             const int tx = t / 9 - 1, ty = (t / 3) % 3 - 1, tz = t % 3 - 1;
+#endif
                             s += w[((long)o * cin + c) * 27 + t] * x[c * V + vox(n, px + tx, py + ty, pz + tz)];
                         }
                     y[o * V + vox(n, px, py, pz)] = s;
@@ -99,7 +110,11 @@ int or_conv3d_bwd(int n, int cin, int cout, const double *x, const double *w, co
  * Phi(x) + x phi(x), phi(x) = exp(-x^2/2) / sqrt(2 pi). */
 static double gelu(double x) { return 0.5 * x * (1.0 + erf(x / sqrt(2.0))); }
 static double gelu_d(double x) {
+#if OR_MUTANT == 9 /* planted: the x phi(x) term of the derivative dropped */
+    return 0.5 * (1.0 + erf(x / sqrt(2.0)));
+#else
     return 0.5 * (1.0 + erf(x / sqrt(2.0))) + x * exp(-0.5 * x * x) / sqrt(2.0 * M_PI);
+#endif
 }
 
 int or_gelu(long count, const double *x, double *y, double *dydx) {
@@ -198,7 +213,11 @@ int or_les_inputs(int N, const double *uhat, int n, double *ubar_hat, double *g,
                     for (int iz = 0; iz < nh; ++iz) {
                         const int k[3] = {wn(ix, n), wn(iy, n), iz};
                         const long m = ((long)ix * n + iy) * nh + iz;
+#if OR_MUTANT == 13 /* planted: transposed gradient, g[3i+j] = d_i u_j */
+                        tmp[m] = I * (double)k[i] * Ub[j * ns + m];
+#else
                         tmp[m] = I * (double)k[j] * Ub[i * ns + m];
+#endif
                     }
             rc = or_irfftn(n, (const double *)tmp, g + (3 * i + j) * np);
         }
@@ -219,7 +238,11 @@ int or_les_inputs(int N, const double *uhat, int n, double *ubar_hat, double *g,
                     pb[((long)ix * n + iy) * nh + iz] = scale * ph[((long)((kx + N) % N) * N + (ky + N) % N) * Nh + kz];
                 }
         rc = or_irfftn(n, (const double *)pb, pf);
+#if OR_MUTANT == 10 /* planted: tau = filt(u_i u_j) + ubar_i ubar_j */
+        for (long p = 0; !rc && p < np; ++p) tau[q * np + p] = pf[p] + ub[pi[q] * np + p] * ub[pj[q] * np + p];
+#else
         for (long p = 0; !rc && p < np; ++p) tau[q * np + p] = pf[p] - ub[pi[q] * np + p] * ub[pj[q] * np + p];
+#endif
     }
     free(tmp);
     free(ub);
@@ -254,7 +277,11 @@ int or_rhs_les(int n, double nu, const double *ubar_hat, const double *tau, doub
                     cplx f[3];
                     for (int i = 0; i < 3; ++i) {
                         f[i] = 0.0;
+#if OR_MUTANT == 11 /* planted: closure term +i k_j tau_ij instead of -i k_j tau_ij */
+                        for (int j = 0; j < 3; ++j) f[i] += I * (double)k[j] * th[idx[i][j] * ns + m];
+#else
                         for (int j = 0; j < 3; ++j) f[i] += -I * (double)k[j] * th[idx[i][j] * ns + m];
+#endif
                     }
                     const double k2 = (double)k[0] * k[0] + (double)k[1] * k[1] + (double)k[2] * k[2];
                     const cplx kf = k[0] * f[0] + k[1] * f[1] + k[2] * f[2];
@@ -279,7 +306,11 @@ int or_smagorinsky(long np, const double *g, double cs_delta2, double *tau) {
         for (int i = 0; i < 3; ++i)
             for (int j = 0; j < 3; ++j) ss += S[i][j] * S[i][j];
         const double mag = sqrt(2.0 * ss);
+#if OR_MUTANT == 12 /* planted: the factor 2 of the eddy-viscosity stress dropped */
+        for (int q = 0; q < 6; ++q) tau[q * np + p] = -cs_delta2 * mag * S[pi[q]][pj[q]];
+#else
         for (int q = 0; q < 6; ++q) tau[q * np + p] = -2.0 * cs_delta2 * mag * S[pi[q]][pj[q]];
+#endif
     }
     return 0;
 }

@@ -211,3 +211,29 @@ def test_closure_energy_rate_identity(orc):
     expect = -(cs * delta) ** 2 * np.mean(mag ** 3)
     got = rate(orc.rhs_les(ub, nu, ts) - base)
     assert expect < 0 and abs(got - expect) < 1e-11 * abs(expect)
+
+
+# ---------------------------------------------------------------- planted mistakes
+def _les_pins():
+    return [test_conv_delta_kernels_shift_and_copy, test_conv_backward_matches_central_differences,
+            test_gelu_closed_form_and_derivative, test_network_gradients_match_central_differences,
+            test_les_stress_of_a_single_mode, test_les_stress_vanishes_for_band_limited_fields,
+            test_les_gradients_of_taylor_green, test_les_rhs_closure_term_closed_form,
+            test_smagorinsky_plane_shear_closed_form, test_smagorinsky_invariants,
+            test_closure_energy_rate_identity]
+
+
+@pytest.mark.parametrize("mutant", [8, 9, 10, 11, 12, 13])
+def test_planted_les_mistakes_are_caught(mutant):
+    # flipped convolution taps, GELU' without x phi(x), tau with the wrong sign
+    # of ubar_i ubar_j, closure term of the wrong sign, Smagorinsky without its
+    # factor 2, transposed velocity gradient: each fails at least one pin
+    import oracle
+    o = oracle.load_mutant(mutant)
+    caught = []
+    for pin in _les_pins():
+        try:
+            pin(o)
+        except AssertionError:
+            caught.append(pin.__name__)
+    assert caught, f"mutant {mutant} passed every LES pin"
