@@ -190,7 +190,7 @@ def test_closure_energy_rate_identity(orc):
     k = np.fft.fftfreq(n, 1.0 / n)
     kz = np.arange(n // 2 + 1)
     KX, KY, KZ = np.meshgrid(k, k, kz, indexing="ij")
-    g = np.stack([np.fft.irfftn(1j * kj * ub[i], s=(n, n, n)) for i in range(3) for kj in (KX, KY, KZ)])
+    g = np.stack([np.fft.irfftn(1j * kj * ub[i], s=(n, n, n), axes=(0, 1, 2)) for i in range(3) for kj in (KX, KY, KZ)])
     w = np.where((KZ == 0) | (KZ == n // 2), 1.0, 2.0)
 
     def rate(du):
