@@ -82,7 +82,8 @@ def recorded_traffic(N, kernel, variant):
     with another launch variant of this pass."""
     path = os.path.join(ROOT, "profiles", f"dram_fp32_{N}.txt")
     try:
-        lines = open(path).read().splitlines()
+        with open(path) as f:
+            lines = f.read().splitlines()
     except OSError:
         return None
     src = [l.split()[1] for l in lines if l.startswith("source_sha256:")]

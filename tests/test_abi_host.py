@@ -13,7 +13,8 @@ HEADER = os.path.join(ROOT, "include", "dns.h")
 
 
 def declared_symbols():
-    text = open(HEADER).read()
+    with open(HEADER) as f:
+        text = f.read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(dns_[a-z0-9_]+)\s*\(", text)))
 
