@@ -285,6 +285,29 @@ def test_checkpoint_resume_is_bit_exact(dns, dtype):
         assert s.time()[1] == 7
 
 
+@pytest.mark.parametrize("dtype", DTYPES, ids=DNAME.get)
+def test_checkpoint_file_resume_is_bit_exact(dns, dtype, tmp_path):
+    # the same resume through a checkpoint file (state, t and step)
+    from paper_1607_00850_gb300 import checkpoint
+    N, nu, dt = 32, 0.01, 0.005
+    uh = inputs.random_isotropic(N, seed=13)
+    with dns.Solver(N, nu, dt, dtype) as s:
+        s.set_velocity(uh)
+        s.step(7)
+        full = s.get_velocity()
+    path = tmp_path / "state.ckpt"
+    with dns.Solver(N, nu, dt, dtype) as s:
+        s.set_velocity(uh)
+        s.step(4)
+        checkpoint.save(s, path)
+    with dns.Solver(N, nu, dt, dtype) as s:
+        meta = checkpoint.restore(s, path)
+        assert meta["step"] == 4 and meta["N"] == N and meta["dtype"] == dtype
+        s.step(3)
+        assert np.array_equal(s.get_velocity(), full)
+        assert s.time()[1] == 7
+
+
 # ---------------------------------------------------------------- state I/O and diagnostics
 @pytest.mark.parametrize("dtype", DTYPES, ids=DNAME.get)
 def test_set_get_roundtrip_and_mask_on_entry(dns, dtype):
