@@ -313,10 +313,11 @@ int dns_les_set_closure_stages(dns_handle h, int every_stage);
 /* ------------------------------------------------------------------------
  * Diagnostics without allocation.  The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc where they need the
- * numbers, such as code running while a stream is captured into a CUDA
- * graph (allocation is not allowed during capture), callbacks and real-time
- * loops that must stay out of the allocator, or processes whose device
- * memory budget belongs to another framework.
+ * numbers, such as callbacks and real-time loops that must stay out of the
+ * allocator (a device allocation can synchronise the device or block), or
+ * processes whose device memory belongs to another framework's pool or
+ * budget, so that memory obtained behind that framework's back could push it
+ * out of memory.
  *
  * Kinetic energy out[0] = <|u|^2>/2 and dissipation out[1] = nu <|grad u|^2>
  * of a full-layout spectral field uhat on the device (mesh N, I/O type of

@@ -2,10 +2,10 @@
 // allocation (dns_energy_noalloc in include/dns.h).
 //
 // Some callers cannot allocate device memory at the point where they need
-// these diagnostics: code that runs while a stream is being captured into a
-// CUDA graph (cudaMalloc is not allowed during capture), callbacks and
-// real-time loops that must not enter the allocator, or processes that run
-// under a fixed memory budget owned by another framework.  This entry point
+// these diagnostics: callbacks and real-time loops that must not enter the
+// allocator (a device allocation can synchronise the device or block), or
+// processes whose device memory is a fixed budget or pool owned by another
+// framework.  This entry point
 // keeps its scratch (one pair of partial sums per kx plane) in a file-scope
 // device array, so it allocates nothing and needs no handle.
 //

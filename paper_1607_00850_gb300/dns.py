@@ -253,19 +253,36 @@ def dns_strerror(status: int) -> str:
 
 def dns_energy_noalloc(N: int, dtype: int, uhat, nu: float, out=None, stream: int | None = None):
     """(E, eps) of a device-resident full-layout field with no device allocation.
-    ``out`` None: results come back to the host; a CUDA float64 tensor of 2
-    elements: results are written there asynchronously."""
-    p, dev, _keep = _buf(uhat)
-    if not dev:
-        raise ValueError("uhat must be device memory")
+    ``out`` None: results come back to the host; a CUDA float64 tensor of at
+    least 2 elements on uhat's device: results are written there
+    asynchronously.  The C entry point cannot see buffer sizes, so the field's
+    element count and type and the output tensor are checked here (ValueError)
+    before anything reaches the device."""
+    N, dtype = int(N), int(dtype)
+    if not (hasattr(uhat, "data_ptr") and hasattr(uhat, "is_cuda")) or not uhat.is_cuda:
+        raise ValueError("uhat must be a CUDA tensor (device memory)")
+    if not uhat.is_contiguous():
+        raise ValueError("uhat must be contiguous")
+    want_type = "complex64" if dtype == DNS_F32 else "complex128"
+    if str(uhat.dtype).rsplit(".", 1)[-1] != want_type:
+        raise ValueError(f"uhat must be {want_type} for dtype {dtype}, got {uhat.dtype}")
+    if N >= 2 and uhat.numel() != 3 * N * N * (N // 2 + 1):
+        raise ValueError(f"uhat has {uhat.numel()} elements, the full layout of N={N} has "
+                         f"{3 * N * N * (N // 2 + 1)}")
+    p = uhat.data_ptr()
     if out is None:
         res = (ctypes.c_double * 2)()
-        _check(load().dns_energy_noalloc(int(N), int(dtype), p, float(nu), res, 0, stream or None),
+        _check(load().dns_energy_noalloc(N, dtype, p, float(nu), res, 0, stream or None),
                "dns_energy_noalloc")
         return res[0], res[1]
-    po, do, _k2 = _buf(out, writable=True)
-    _check(load().dns_energy_noalloc(int(N), int(dtype), p, float(nu), ctypes.cast(po, _dp), do, stream or None),
-           "dns_energy_noalloc")
+    if not (hasattr(out, "data_ptr") and hasattr(out, "is_cuda")) or not out.is_cuda:
+        raise ValueError("out must be a CUDA float64 tensor (or None for a host result)")
+    if str(out.dtype).rsplit(".", 1)[-1] != "float64" or not out.is_contiguous() or out.numel() < 2:
+        raise ValueError("out must be a contiguous float64 tensor of at least 2 elements")
+    if out.device != uhat.device:
+        raise ValueError("out must be on uhat's device")
+    _check(load().dns_energy_noalloc(N, dtype, p, float(nu), ctypes.cast(out.data_ptr(), _dp), 1,
+                                     stream or None), "dns_energy_noalloc")
     return out
 
 
@@ -366,6 +383,7 @@ class Solver:
 
     def __init__(self, N: int, nu: float, dt: float, dtype: int = DNS_F32, stream: int | None = None):
         self.N, self.nu, self.dt, self.dtype = int(N), float(nu), float(dt), int(dtype)
+        self.integrator = DNS_RK4
         self._pending = []  # host buffers of queued asynchronous I/O, held until synchronize()
         self.h = dns_init(N, nu, dt, dtype, stream)
 
@@ -430,6 +448,11 @@ class Solver:
 
     def step(self, n: int = 1):
         dns_step(self.h, n)
+
+    def set_integrator(self, kind: int):
+        """DNS_RK4 or DNS_IFRK4 (recorded so checkpoints can carry it)."""
+        dns_set_integrator(self.h, kind)
+        self.integrator = int(kind)
 
     def synchronize(self):
         dns_synchronize(self.h)

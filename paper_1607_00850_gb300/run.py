@@ -39,18 +39,21 @@ def diagnostics(solver, spectrum: bool) -> dict:
 
 
 def run(solver, steps: int, every: int, log, ckpt_path=None, ckpt_every: int = 0, spectrum: bool = False,
-        clock=time.perf_counter) -> int:
+        clock=time.perf_counter, first_row: bool = True) -> int:
     """Advance `solver` to step `steps` (counting from its current step),
     writing diagnostics every `every` steps to the text stream `log` and a
     checkpoint every `ckpt_every` steps (0: only at the end) when ckpt_path
-    is set.  Returns the final step."""
+    is set.  `first_row` writes a row for the starting state; a resumed run
+    leaves it out, since the log it appends to already holds that step.
+    wall_s counts from the start of this call.  Returns the final step."""
     if every < 1:
         raise ValueError("every must be >= 1")
     _, start = solver.time()
     t0 = clock()
-    row = diagnostics(solver, spectrum)
-    row["wall_s"] = 0.0
-    log.write(json.dumps(row) + "\n")
+    if first_row:
+        row = diagnostics(solver, spectrum)
+        row["wall_s"] = 0.0
+        log.write(json.dumps(row) + "\n")
     done = start
     while done < steps:
         n = min(every - (done % every), steps - done)
@@ -87,6 +90,8 @@ def main(argv=None) -> int:
     p.add_argument("--checkpoint", default=None)
     p.add_argument("--checkpoint-every", type=int, default=0)
     p.add_argument("--resume", action="store_true")
+    p.add_argument("--allow-parameter-change", action="store_true",
+                   help="resume with --nu/--dt/--ifrk4 that differ from the checkpoint's")
     a = p.parse_args(argv)
     from . import dns
     dtype = dns.DTYPE_NAMES[a.dtype]
@@ -94,14 +99,14 @@ def main(argv=None) -> int:
     try:
         with dns.Solver(a.N, a.nu, a.dt, dtype) as s:
             if a.ifrk4:
-                dns.dns_set_integrator(s.h, dns.DNS_IFRK4)
+                s.set_integrator(dns.DNS_IFRK4)
             if a.resume:
                 if not a.checkpoint or not os.path.exists(a.checkpoint):
                     raise SystemExit("--resume needs an existing --checkpoint file")
-                checkpoint.restore(s, a.checkpoint)
+                checkpoint.restore(s, a.checkpoint, allow_parameter_change=a.allow_parameter_change)
             else:
                 s.set_velocity(initial_field(a.init, a.N, a.seed, a.k0))
-            run(s, a.steps, a.every, log, a.checkpoint, a.checkpoint_every, a.spectrum)
+            run(s, a.steps, a.every, log, a.checkpoint, a.checkpoint_every, a.spectrum, first_row=not a.resume)
     finally:
         if log is not sys.stdout:
             log.close()

@@ -81,3 +81,49 @@ def test_supported_sizes_match_plan():
     for n in dns.SUPPORTED_N:
         m = n // 3 if n % 3 == 0 else n
         assert m & (m - 1) == 0 and n % 2 == 0
+
+
+class _FakeDeviceTensor:
+    """Enough of a CUDA tensor's surface for the wrapper's checks; its
+    pointer is never passed on, since every case below is rejected first."""
+
+    def __init__(self, dtype, numel, contiguous=True, device="cuda:0"):
+        self.dtype, self._numel, self._contig, self.device = dtype, numel, contiguous, device
+        self.is_cuda = True
+
+    def data_ptr(self):
+        return 0x1000
+
+    def numel(self):
+        return self._numel
+
+    def is_contiguous(self):
+        return self._contig
+
+
+def test_noalloc_wrapper_rejects_mismatched_buffers():
+    # the C entry point cannot see buffer sizes: the binding checks the field's
+    # element count and type and the output tensor before anything runs
+    torch = pytest.importorskip("torch")
+    from paper_1607_00850_gb300 import dns
+    N = 16
+    n = 3 * N * N * (N // 2 + 1)
+    good32 = _FakeDeviceTensor(torch.complex64, n)
+    with pytest.raises(ValueError, match="CUDA"):
+        dns.dns_energy_noalloc(N, dns.DNS_F32, torch.zeros(n, dtype=torch.complex64), 0.01)
+    with pytest.raises(ValueError, match="complex128"):
+        dns.dns_energy_noalloc(N, dns.DNS_F64, good32, 0.01)
+    with pytest.raises(ValueError, match="complex128"):
+        dns.dns_energy_noalloc(N, dns.DNS_F32_ACC64, good32, 0.01)
+    with pytest.raises(ValueError, match="complex64"):
+        dns.dns_energy_noalloc(N, dns.DNS_F32, _FakeDeviceTensor(torch.complex128, n), 0.01)
+    with pytest.raises(ValueError, match="elements"):
+        dns.dns_energy_noalloc(N, dns.DNS_F32, _FakeDeviceTensor(torch.complex64, n - 1), 0.01)
+    with pytest.raises(ValueError, match="contiguous"):
+        dns.dns_energy_noalloc(N, dns.DNS_F32, _FakeDeviceTensor(torch.complex64, n, contiguous=False), 0.01)
+    for bad_out in (torch.zeros(2, dtype=torch.float64),                         # host tensor
+                    _FakeDeviceTensor(torch.float32, 2),                         # wrong type
+                    _FakeDeviceTensor(torch.float64, 1),                         # too small
+                    _FakeDeviceTensor(torch.float64, 2, device="cuda:1")):       # other device
+        with pytest.raises(ValueError, match="out"):
+            dns.dns_energy_noalloc(N, dns.DNS_F32, good32, 0.01, out=bad_out)

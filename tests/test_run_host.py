@@ -88,6 +88,13 @@ def test_continuation_counts_from_the_current_step():
         run.run(s, 40, 0, log)
 
 
+def test_resumed_run_writes_no_duplicate_first_row():
+    s, log = FakeSolver(), io.StringIO()
+    s.step(12)
+    run.run(s, 30, 10, log, first_row=False)
+    assert [x["step"] for x in rows(log)] == [20, 30]
+
+
 def test_initial_fields():
     assert run.initial_field("tg", 8, 0, 4.0).shape == (3, 8, 8, 5)
     assert run.initial_field("isotropic", 8, 1, 2.0).shape == (3, 8, 8, 5)

@@ -1,8 +1,9 @@
 """The allocation-free diagnostics entry point (dns_energy_noalloc).
 
 Some callers cannot call cudaMalloc where they need the energy and the
-dissipation (inside a CUDA-graph capture, in callbacks or allocator-free
-loops, under a memory budget owned by another framework).  This test calls
+dissipation: callbacks and real-time loops that must stay out of the
+allocator, or processes whose device memory is a budget owned by another
+framework.  This test calls
 that entry point through the C ABI twice in a row and checks both results
 against the handle-based dns_energy / dns_dissipation within the FP64
 diagnostics tolerance of the other tests, for host and device outputs.  It
