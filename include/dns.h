@@ -336,6 +336,17 @@ int dns_les_set_closure_stages(dns_handle h, int every_stage);
 int dns_energy_noalloc(int N, int dtype, const void *uhat, double nu, double *out, int out_on_device,
                        void *cuda_stream);
 
+/* ------------------------------------------------------------------------
+ * Measurement utility (the paper has no counterpart): the FP64 arithmetic
+ * peak of the current device, as the denominator of the FP64 path's
+ * roofline.  Runs a kernel of independent FP64 fused multiply-adds over
+ * every SM for about `seconds` (0 < seconds <= 10, else DNS_ERR_ARG) on the
+ * default stream, synchronises, and writes the achieved rate in TFLOP/s (two
+ * flops per FMA) to *tflops (host memory).  Allocates nothing; DNS_ERR_CUDA
+ * on a launch or event error.
+ * ------------------------------------------------------------------------ */
+int dns_fp64_fma_rate(double seconds, double *tflops);
+
 /* Human-readable name of a status code (static storage). */
 const char *dns_strerror(int status);
 

@@ -55,7 +55,8 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     os.makedirs(BUILD, exist_ok=True)
     units = [(os.path.join(CSRC, "dns_api.cu"), os.path.join(BUILD, "dns_api.o"), ()),
              (os.path.join(CSRC, "dns_noalloc.cu"), os.path.join(BUILD, "dns_noalloc.o"), ()),
-             (os.path.join(CSRC, "dns_les.cu"), os.path.join(BUILD, "dns_les.o"), ())]
+             (os.path.join(CSRC, "dns_les.cu"), os.path.join(BUILD, "dns_les.o"), ()),
+             (os.path.join(CSRC, "dns_peak.cu"), os.path.join(BUILD, "dns_peak.o"), ())]
     for n in SIZES:
         units.append((os.path.join(CSRC, "dns_inst.cu"), os.path.join(BUILD, f"dns_inst_{n}.o"),
                       (f"-DDNS_N={n}",)))

@@ -238,6 +238,23 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
 }
 
 // ------------------------------------------------------------------- P3
+// Pairs of real fields packed into the three complex lines of the inverse
+// (B fields 0..2 = u, 3..5 = omega): (ux, uy), (uz, wz), (wx, wy).  Rounding
+// in a packed transform leaks a relative O(eps) part of each field of a
+// pair into the other; u x omega has no product u_i w_i, so with these pairs
+// the leak never forms a square (with (uz, wx), uz wx would gain
+// eps (wx^2 - uz^2), a sign-definite error that adds up coherently over the
+// x-y planes and shows in the (0, 0, kz) modes of the nonlinear term).  The
+// mixed pair carries wz / S, S a power of two near the ratio of the two
+// fields' magnitudes, so neither field's leak is amplified by |w| / |u|;
+// the physical wz is multiplied back by S (both scalings are exact).
+template <int N> struct P3Pairs {
+    static constexpr int K = (N - 1) / 3;
+    static constexpr double S = K >= 128 ? 32.0 : (K >= 32 ? 16.0 : (K >= 8 ? 8.0 : 2.0));
+    static __host__ __device__ constexpr int fa(int p) { return p == 0 ? 0 : (p == 1 ? 2 : 3); }
+    static __host__ __device__ constexpr int fb(int p) { return p == 0 ? 1 : (p == 1 ? 5 : 4); }
+};
+
 // L lines (consecutive y at one x) per block, row-mapped (RowFFT).  Pairs of
 // real fields share one complex transform: virtual line (p, l) holds
 // X_{2p} + i X_{2p+1}, extended to the full length by Hermitian symmetry
@@ -322,11 +339,11 @@ __device__ __forceinline__ void p3_mid_fused(typename CT<real>::t *tile, const t
                 for (int r = 1; r < R; ++r) xp[r] = cmul(xp[r], w[r]);
                 dft<R, +1>(xp);
             }
-            // point z = j + r NB: (ux, uy), (uz, wx), (wy, wz) -> Nx + i Ny, Nz + 0i
+            // point z = j + r NB: (ux, uy), (uz, wz / S), (wx, wy) -> Nx + i Ny, Nz + 0i
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                const real ux = va[q][r].x, uy = va[q][r].y, uz = vb[q][r].x, wx = vb[q][r].y, wy = x2[r].x,
-                           wz = x2[r].y;
+                const real ux = va[q][r].x, uy = va[q][r].y, uz = vb[q][r].x,
+                           wz = vb[q][r].y * (real)P3Pairs<N>::S, wx = x2[r].x, wy = x2[r].y;
                 va[q][r] = cmk<cplx>(uy * wz - uz * wy, uz * wx - ux * wz);
                 vb[q][r] = cmk<cplx>(ux * wy - uy * wx, 0.0);
             }
@@ -373,7 +390,8 @@ __device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>
                 for (int r = 0; r < R; ++r) {
                     const int a = radd(j + r * NB);
                     const cplx p0 = tile[l * LDR + a], p1 = tile[(L + l) * LDR + a], p2 = tile[(2 * L + l) * LDR + a];
-                    const real ux = p0.x, uy = p0.y, uz = p1.x, wx = p1.y, wy = p2.x, wz = p2.y;
+                    const real ux = p0.x, uy = p0.y, uz = p1.x, wz = p1.y * (real)P3Pairs<N>::S, wx = p2.x,
+                               wy = p2.y;
                     va[q][r] = cmk<cplx>(uy * wz - uz * wy, uz * wx - ux * wz);
                     vb[q][r] = cmk<cplx>(ux * wy - uy * wx, 0.0);
                 }
@@ -401,14 +419,16 @@ __device__ __forceinline__ void p3_forward_store(const Geo &g, typename CT<real>
 }
 
 // First-stage input of the packed inverse: virtual line vl = p L + l holds
-// field 2p + i field 2p+1 of line l, Hermitian-extended along z (a, b are
-// the two fields' coefficients at kz = n or N - n).
-template <typename cplx>
-__device__ __forceinline__ cplx p3_pack(cplx a, cplx b, int n, int kz, int N) {
+// field fa(p) + i field fb(p) of line l (fb(1) = wz divided by S),
+// Hermitian-extended along z (a, b are the two fields' coefficients at
+// kz = n or N - n).
+template <int N, typename cplx>
+__device__ __forceinline__ cplx p3_pack(cplx a, cplx b, int p, int n, int kz) {
     if (kz == 0) {
         a.y = 0;
         b.y = 0;
     }
+    if (p == 1) b = cscale(b, (decltype(b.x))(1.0 / P3Pairs<N>::S));
     return n <= N / 2 ? cmk<cplx>(a.x - b.y, a.y + b.x) : cmk<cplx>(a.x + b.y, b.x - a.y);
 }
 
@@ -434,7 +454,7 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
         const int kz = n <= N / 2 ? n : N - n;
         if (kz > K) return cmk<cplx>(0.0, 0.0);
         const long long off = (line0 + l) * Kzp + kz;
-        return p3_pack(B[(2 * p) * sB + off], B[(2 * p + 1) * sB + off], n, kz, N);
+        return p3_pack<N>(B[P3Pairs<N>::fa(p) * sB + off], B[P3Pairs<N>::fb(p) * sB + off], p, n, kz);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
@@ -506,7 +526,7 @@ __device__ __noinline__ void p3_tma_group(Geo g, const typename CT<real>::t *tw,
         const int kz = n <= N / 2 ? n : N - n;
         if (kz > K) return cmk<cplx>(0.0, 0.0);
         const cplx *row = stage + l * PS::KZP + kz;
-        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+        return p3_pack<N>(row[P3Pairs<N>::fa(p) * (L * PS::KZP)], row[P3Pairs<N>::fb(p) * (L * PS::KZP)], p, n, kz);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, true, true>::run(tile, tw, iload, tstore);
@@ -598,7 +618,7 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
         const int kz = n <= N / 2 ? n : N - n;
         if (kz > K) return cmk<cplx>(0.0, 0.0);
         const cplx *row = stage + l * PS::KZP + kz;
-        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+        return p3_pack<N>(row[P3Pairs<N>::fa(p) * (L * PS::KZP)], row[P3Pairs<N>::fb(p) * (L * PS::KZP)], p, n, kz);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
@@ -647,7 +667,7 @@ __device__ __forceinline__ void p3_bulkf_body(Geo g, const typename CT<real>::t 
         const int kz = n <= N / 2 ? n : N - n;
         if (kz > K) return cmk<cplx>(0.0, 0.0);
         const cplx *row = stage + l * PS::KZP + kz;
-        return p3_pack(row[(2 * p) * (L * PS::KZP)], row[(2 * p + 1) * (L * PS::KZP)], n, kz, N);
+        return p3_pack<N>(row[P3Pairs<N>::fa(p) * (L * PS::KZP)], row[P3Pairs<N>::fb(p) * (L * PS::KZP)], p, n, kz);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true, true, true>::run(tile, tw, iload, tstore);

@@ -77,6 +77,7 @@ SIGNATURES = {
     "dns_les_set_closure": (_i, [_vp, _vp]),
     "dns_les_set_smagorinsky": (_i, [_vp, _d, _d]),
     "dns_les_set_closure_stages": (_i, [_vp, _i]),
+    "dns_fp64_fma_rate": (_i, [_d, _dp]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
 }
@@ -245,6 +246,13 @@ def dns_device_bytes(h: int) -> int:
     b = ctypes.c_longlong()
     _check(load().dns_device_bytes(h, ctypes.byref(b)), "dns_device_bytes")
     return b.value
+
+
+def dns_fp64_fma_rate(seconds: float = 1.0) -> float:
+    """Measured FP64 FMA throughput of the current device in TFLOP/s."""
+    v = ctypes.c_double()
+    _check(load().dns_fp64_fma_rate(float(seconds), ctypes.byref(v)), "dns_fp64_fma_rate")
+    return v.value
 
 
 def dns_strerror(status: int) -> str:
