@@ -66,6 +66,8 @@ static bool c2c_supported(int N) { return N == 16 || N == 32 || N == 64 || N == 
 
 static inline unsigned nblk(long long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+constexpr size_t kMaxSmemLes = 226 * 1024;  // dynamic shared memory a block may use (+ its static barriers)
+
 // ---------------------------------------------------------------- network kernels
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_d(float x) {
@@ -380,6 +382,269 @@ template <int CIN, int COUT, int EPI> static cudaError_t conv_tc_attr() {
                                 (int)ConvTc<CIN, COUT>::smem);
 }
 
+// The same convolution on the fifth-generation tensor cores, fed from a
+// shared-memory halo slab instead of per-tap gathers.  A persistent block
+// walks work items (x, y0): Y consecutive z lines (x, y0 .. y0+Y-1).  For an
+// item it lands, by 16-byte cp.async copies (one warp per line), the slab of
+// input rows x-1..x+1, y0-1..y0+Y and z = -1..n (periodic), one row per
+// voxel, in the K-major core-matrix layout [CIN/8 chunks][rows][8 BF16] with
+// the rows of a z line consecutive:
+//   slab row s = (xi (Y+2) + yi) (n+2) + r,  xi, yi, r = x, y, z offsets + 1.
+// Output positions p = yl (n+2) + r run over the item's lines with their
+// two halo rows (invalid outputs, never stored).  The input of tap
+// (dx, dy, dz) for output p is slab row p + (1+dx)(Y+2)(n+2) + (1+dy)(n+2)
+// + dz, a fixed shift for all p: each tap's A operand of an M = 128 tile of
+// positions is the same slab read from a shifted start address, so the 27
+// taps' MMAs (CIN/16 K steps each) of every tile are issued back to back
+// with no gather or barrier between them.  The layer's weights (27 CIN/16
+// tiles of COUT x 16) stay in shared memory for the whole block.
+//
+// Roles: warp 0 issues the MMAs (one thread), warps 1..8 copy slabs and run
+// the epilogue (two groups of four warps, each covering the 128 tensor-
+// memory lanes, take alternate tiles).  Hand-offs are mbarriers:
+//   slab_full[b]  copy warps -> MMA warp: slab buffer b has landed
+//   mma_done[a]   MMA commit -> copy warps: the item's MMAs are complete
+//                 (its slab buffer is free, accumulator a is readable)
+//   acc_free[a]   copy warps -> MMA warp: accumulator a has been read
+// Two slab buffers (one where two do not fit) and two accumulators let the
+// copies of the next item and the epilogue of the previous one run while
+// the current item's MMAs execute.  Every wait is bounded; on expiry the
+// waiting thread records kErrWaitTimeout, every role leaves its loop at its
+// next check, the issued MMAs are waited for (bounded) and the tensor
+// memory is freed.
+struct SlabGeom {
+    int n, Y, rows, tiles, nbuf;
+    size_t slab_bytes, smem;
+};
+
+template <int CIN, int COUT> struct ConvSlab {
+    static constexpr int KS = CIN / 16;         // K steps per tap
+    static constexpr int CH = CIN / 8;          // 16-byte chunks per voxel row
+    static constexpr int BT = COUT / 8 * 256;   // bytes of one B tile (COUT x 16)
+    static constexpr int BBYTES = 27 * KS * BT; // all weights
+    static constexpr int ACC_COLS = 128;        // tensor-memory columns per accumulator buffer
+    static SlabGeom geom(int n) {
+        SlabGeom g{};
+        g.n = n;
+        g.Y = n <= 16 ? 8 : (n <= 64 ? 4 : 1);
+        if (g.Y > n) g.Y = n;
+        g.rows = 3 * (g.Y + 2) * (n + 2) + 2;  // + one padding row at each end
+        g.tiles = (g.Y * (n + 2) + 127) / 128;
+        g.slab_bytes = (size_t)CH * g.rows * 16;
+        const size_t fixed = (size_t)BBYTES + 1024;
+        g.nbuf = fixed + 2 * g.slab_bytes <= kMaxSmemLes ? 2 : 1;
+        // at least 80 KB, so no more than two blocks share an SM: each holds
+        // 256 of the SM's 512 tensor-memory columns
+        g.smem = (size_t)BBYTES + g.nbuf * g.slab_bytes;
+        if (g.smem < 80 * 1024) g.smem = 80 * 1024;
+        return g;
+    }
+};
+
+constexpr int kSlabCopyWarps = 8;                     // copy + epilogue warps (1..8)
+constexpr int kSlabThreads = 32 * (1 + kSlabCopyWarps);  // + the MMA warp (0)
+
+// Bounded mbarrier wait; on expiry marks the block failed (shared flag) and
+// records the timeout.  Returns false if the block has failed.
+__device__ __forceinline__ bool slab_wait(uint64_t *bar, uint32_t parity, volatile int *ok, int *err) {
+    if (!*ok) return false;
+    if (mbar_wait_bounded(bar, parity)) return true;
+    *ok = 0;
+    record_error(err, kErrWaitTimeout);
+    return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <int CIN, int COUT, int EPI>
+__global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, const __nv_bfloat16 *__restrict__ X,
+                                                              const __nv_bfloat16 *__restrict__ Wc,
+                                                              const float *__restrict__ bias, float *__restrict__ Z,
+                                                              __nv_bfloat16 *__restrict__ A,
+                                                              const float *__restrict__ Zp, int *err) {
+    typedef ConvSlab<CIN, COUT> C;
+    constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, COUT);
+    constexpr uint32_t TCOLS = 2 * C::ACC_COLS;
+    constexpr int NCOPY = 32 * kSlabCopyWarps;
+    static_assert(COUT == 16 || COUT == 32, "one or two 16-column accumulator loads");
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char *sB = smem_raw;
+    unsigned char *sSlab = smem_raw + C::BBYTES;
+    __shared__ __align__(8) uint64_t slab_full[2], mma_done[2], acc_free[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ volatile int s_ok;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int n = sg.n, Y = sg.Y, L = n + 2, rows = sg.rows;
+    const int plane = (Y + 2) * L;  // slab rows per x plane
+    const int ybl = n / Y;          // items per x plane
+    const long long items = (long long)n * ybl;
+    const int nbuf = sg.nbuf;
+
+    for (int e = tid; e < C::BBYTES / 16; e += kSlabThreads)
+        reinterpret_cast<uint4 *>(sB)[e] = reinterpret_cast<const uint4 *>(Wc)[e];
+    fence_proxy_async_smem();  // the weights are read by the MMAs (async proxy)
+    if (tid == 0) {
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&slab_full[i], NCOPY);
+            mbar_init(&mma_done[i], 1);
+            mbar_init(&acc_free[i], NCOPY);
+        }
+        s_ok = 1;
+    }
+    if (warp == 0) tc::tmem_alloc(&tmem_base, TCOLS);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const long long first = blockIdx.x, stride = gridDim.x;
+    const int nitems = first < items ? (int)((items - 1 - first) / stride + 1) : 0;
+
+    if (warp == 0) {
+        // ---------------- MMA warp: one thread issues, the warp stays converged
+        int committed = -1;
+        if (lane == 0) {
+            const uint32_t lbo16 = (uint32_t)rows;  // K-adjacent core matrices: next chunk (rows x 16 B) >> 4
+            const uint64_t bdesc0 = tc::smem_desc(sB, 128, 256);
+            const int npos = Y * L;
+            for (int j = 0; j < nitems; ++j) {
+                const int b = nbuf == 2 ? (j & 1) : 0;
+                const uint32_t ub = nbuf == 2 ? (uint32_t)(j >> 1) : (uint32_t)j;  // uses of slab buffer b
+                if (!slab_wait(&slab_full[b], ub & 1, &s_ok, err)) break;
+                if (j >= 2 && !slab_wait(&acc_free[j & 1], (uint32_t)(((j - 2) >> 1) & 1), &s_ok, err)) break;
+                tc::fence_after_sync();
+                // A descriptor of slab row 0 of buffer b (after the front padding row)
+                const uint32_t a0 = smem_addr(sSlab + (size_t)b * sg.slab_bytes) + 16;
+                const uint64_t adesc0 = (uint64_t)((a0 & 0x3FFFFu) >> 4) | ((uint64_t)(lbo16 & 0x3FFFu) << 16) |
+                                        ((uint64_t)(128 >> 4) << 32) | (1ull << 46);
+                const uint32_t tacc = tmem_base + (uint32_t)((j & 1) * C::ACC_COLS);
+                for (int t = 0; t < sg.tiles; ++t) {
+                    const int p0 = min(128 * t, npos - 128);
+#pragma unroll
+                    for (int tap = 0; tap < 27; ++tap) {
+                        const int dx = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dz = tap % 3 - 1;
+                        // slab row of output p0 for this tap, in 16-byte units (-1 for the
+                        // first tap of the first tile: the front padding row); signed, so
+                        // the sum with the descriptor's address field never borrows
+                        const int row = p0 + dz + (1 + dx) * plane + (1 + dy) * L;
+#pragma unroll
+                        for (int kk = 0; kk < C::KS; ++kk) {
+                            const uint64_t adesc = (uint64_t)((long long)adesc0 + (long long)(row + 2 * kk * rows));
+                            const uint64_t bdesc = bdesc0 + (uint64_t)(((tap * C::KS + kk) * C::BT) >> 4);
+                            tc::mma_bf16(tacc + t * COUT, adesc, bdesc, IDESC, tap > 0 || kk > 0);
+                        }
+                    }
+                }
+                tc::commit(&mma_done[j & 1]);
+                committed = j;
+            }
+            if (!s_ok && committed >= 0)  // let the issued MMAs finish before the memory is freed
+                mbar_wait_bounded(&mma_done[committed & 1], (uint32_t)((committed >> 1) & 1));
+        }
+        __syncwarp();
+    } else {
+        // ---------------- copy + epilogue warps
+        const int cw = warp - 1;         // 0..7
+        const int wq = warp & 3;         // tensor-memory lane quadrant this warp may read
+        const int grp = cw >> 2;         // tiles t = grp, grp + 2, ...
+        auto gather = [&](long long w, int b) {
+            const int x = (int)(w / ybl), y0 = (int)(w % ybl) * Y;
+            unsigned char *dst = sSlab + (size_t)b * sg.slab_bytes;
+            const int nlines = 3 * (Y + 2);
+            for (int li = cw; li < nlines; li += kSlabCopyWarps) {
+                const int xi = li / (Y + 2), yi = li % (Y + 2);
+                const int gx = (x - 1 + xi + n) % n, gy = (y0 - 1 + yi + n) % n;
+                const __nv_bfloat16 *src = X + ((long long)gx * n + gy) * n * CIN;
+                unsigned char *d = dst + ((size_t)li * L + 1) * 16;  // + the front padding row
+                for (int e = lane; e < L * C::CH; e += 32) {
+                    const int r = e / C::CH, c = e % C::CH;
+                    const int z = r == 0 ? n - 1 : (r == n + 1 ? 0 : r - 1);
+                    cp_async16(d + ((size_t)c * rows + r) * 16, src + (long long)z * CIN + 8 * c);
+                }
+            }
+            cp_async_commit();
+        };
+        auto epilogue = [&](long long w, int j) {
+            const int x = (int)(w / ybl), y0 = (int)(w % ybl) * Y;
+            const uint32_t tacc = tmem_base + (uint32_t)((j & 1) * C::ACC_COLS) + ((uint32_t)(32 * wq) << 16);
+            const int npos = Y * L;
+            for (int t = grp; t < sg.tiles; t += 2) {
+                const int p0 = min(128 * t, npos - 128);
+                const int p = p0 + 32 * wq + lane;
+                float acc[COUT];
+                tc::ld16(tacc + t * COUT, *reinterpret_cast<float(*)[16]>(acc));
+                if constexpr (COUT == 32) tc::ld16(tacc + t * COUT + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
+                const int yl = p / L, z = p % L - 1;
+                if (p < 128 * t || z < 0 || z >= n) continue;  // halo row, or computed by the previous tile
+                const long long v = ((long long)x * n + (y0 + yl)) * n + z;
+#pragma unroll
+                for (int o = 0; o < COUT; o += 2) {
+                    float y0v = acc[o], y1v = acc[o + 1];
+                    if (bias) {
+                        y0v += bias[o];
+                        y1v += bias[o + 1];
+                    }
+                    if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT)
+                        *reinterpret_cast<float2 *>(Z + v * COUT + o) = make_float2(y0v, y1v);
+                    if constexpr (EPI == EPI_HIDDEN)
+                        *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
+                            __floats2bfloat162_rn(gelu_f(y0v), gelu_f(y1v));
+                    if constexpr (EPI == EPI_DGRAD) {
+                        const float2 zp = *reinterpret_cast<const float2 *>(Zp + v * COUT + o);
+                        *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
+                            __floats2bfloat162_rn(y0v * gelu_d(zp.x), y1v * gelu_d(zp.y));
+                    }
+                }
+            }
+        };
+        for (int j = 0; j <= nitems; ++j) {
+            if (j < nitems) {
+                const int b = nbuf == 2 ? (j & 1) : 0;
+                // the buffer was last read by the MMAs of item j - nbuf
+                const int jb = j - nbuf;
+                if (jb >= 0 && !slab_wait(&mma_done[jb & 1], (uint32_t)((jb >> 1) & 1), &s_ok, err)) break;
+                gather(first + (long long)j * stride, b);
+                cp_async_wait<0>();
+                fence_proxy_async_smem();
+                mbar_arrive(&slab_full[b]);
+            }
+            if (j >= 1) {
+                const int je = j - 1;
+                if (!slab_wait(&mma_done[je & 1], (uint32_t)((je >> 1) & 1), &s_ok, err)) break;
+                tc::fence_after_sync();
+                epilogue(first + (long long)je * stride, je);
+                tc::fence_before_sync();
+                mbar_arrive(&acc_free[je & 1]);
+            }
+        }
+        cp_async_wait<0>();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem_base, TCOLS);
+}
+
+template <int CIN, int COUT, int EPI>
+static cudaError_t conv_slab(int n, const __nv_bfloat16 *X, const __nv_bfloat16 *Wc, const float *bias, float *Z,
+                             __nv_bfloat16 *A, const float *Zp, int *err, cudaStream_t st) {
+    const SlabGeom g = ConvSlab<CIN, COUT>::geom(n);
+    if (g.Y * (n + 2) < 128 || g.tiles * COUT > ConvSlab<CIN, COUT>::ACC_COLS || g.smem > kMaxSmemLes)
+        return cudaErrorInvalidValue;
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const long long items = (long long)n * (n / g.Y);
+    const unsigned grid = (unsigned)(items < sms ? items : sms);
+    k_conv_slab<CIN, COUT, EPI><<<grid, kSlabThreads, g.smem, st>>>(g, X, Wc, bias, Z, A, Zp, err);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int EPI> static cudaError_t conv_slab_attr() {
+    return cudaFuncSetAttribute(k_conv_slab<CIN, COUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kMaxSmemLes);
+}
+
 // Weight gradient partials: block (chunk, tap) accumulates
 // D[o][c] = sum_{v in chunk} dY[v][o] X[v + off(t)][c] (M = COUTP rows o,
 // N = CIN cols c, K = voxels) and writes it to P[chunk][t][o][c].  COUTP is
@@ -633,6 +898,8 @@ static cudaError_t conv_layer(dns_net_ctx *c, const __nv_bfloat16 *X, const __nv
                               const __nv_bfloat16 *Wc, const float *bias, float *Z, __nv_bfloat16 *A, const float *Zp,
                               cudaStream_t st) {
     if (c->engine == DNS_CONV_TCGEN05) return conv_tc<CIN, COUT, EPI>(c->n, X, Wc, bias, Z, A, Zp, c->err, st);
+    if (c->engine == DNS_CONV_TCGEN05_SLAB)
+        return conv_slab<CIN, COUT, EPI>(c->n, X, Wc, bias, Z, A, Zp, c->err, st);
     return conv<CIN, COUT, EPI>(c->n, X, W, bias, Z, A, Zp, st);
 }
 
@@ -789,6 +1056,9 @@ int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *o
         cudaMemset(c->err, 0, sizeof(int)) != cudaSuccess || conv_tc_attr<16, 32, EPI_HIDDEN>() != cudaSuccess ||
         conv_tc_attr<32, 32, EPI_HIDDEN>() != cudaSuccess || conv_tc_attr<32, OUTP, EPI_OUT>() != cudaSuccess ||
         conv_tc_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess || conv_tc_attr<32, 32, EPI_DGRAD>() != cudaSuccess ||
+        conv_slab_attr<16, 32, EPI_HIDDEN>() != cudaSuccess || conv_slab_attr<32, 32, EPI_HIDDEN>() != cudaSuccess ||
+        conv_slab_attr<32, OUTP, EPI_OUT>() != cudaSuccess || conv_slab_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess ||
+        conv_slab_attr<32, 32, EPI_DGRAD>() != cudaSuccess ||
         conv_attr<16, 32, EPI_HIDDEN>() != cudaSuccess || conv_attr<32, 32, EPI_HIDDEN>() != cudaSuccess ||
         conv_attr<32, OUTP, EPI_OUT>() != cudaSuccess || conv_attr<OUTP, 32, EPI_DGRAD>() != cudaSuccess ||
         conv_attr<32, 32, EPI_DGRAD>() != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) {
@@ -809,7 +1079,8 @@ int dns_net_free(dns_net net) {
 long dns_net_param_count(void) { return NET_PARAMS; }
 
 int dns_net_set_engine(dns_net net, int engine) {
-    if (!net || (engine != DNS_CONV_MMA_SYNC && engine != DNS_CONV_TCGEN05)) return DNS_ERR_ARG;
+    if (!net || (engine != DNS_CONV_MMA_SYNC && engine != DNS_CONV_TCGEN05 && engine != DNS_CONV_TCGEN05_SLAB))
+        return DNS_ERR_ARG;
     net->engine = engine;
     return DNS_OK;
 }

@@ -555,7 +555,7 @@ def dns_net_param_count() -> int:
     return int(load().dns_net_param_count())
 
 
-DNS_CONV_MMA_SYNC, DNS_CONV_TCGEN05 = 0, 1
+DNS_CONV_MMA_SYNC, DNS_CONV_TCGEN05, DNS_CONV_TCGEN05_SLAB = 0, 1, 2
 
 
 def dns_net_set_engine(net: int, engine: int) -> None:

@@ -284,6 +284,7 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
     dev = torch.device("cuda")
     flops = 2.0 * n ** 3 * 27 * (9 * 32 + 32 * 32 + 32 * 6)
     net = dns.dns_net_create(n, seed=1)
+    default_engine = dns.dns_net_get_engine(net)
     out = {"n": n, "forward_flops": flops}
     try:
         gen = torch.Generator(device=dev).manual_seed(7)
@@ -307,8 +308,18 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
         fwd_tc = time_forward()
         out["forward_ms_tcgen05"] = fwd_tc
         out["forward_tflops_tcgen05"] = flops / (fwd_tc / 1e3) / 1e12
+        dns.dns_net_set_engine(net, dns.DNS_CONV_TCGEN05_SLAB)
+        fwd_slab = time_forward()
+        out["forward_ms_tcgen05_slab"] = fwd_slab
+        out["forward_tflops_tcgen05_slab"] = flops / (fwd_slab / 1e3) / 1e12
         dns.dns_net_set_engine(net, dns.DNS_CONV_MMA_SYNC)
         fwd = time_forward()
+        out["forward_ms_mma_sync"] = fwd
+        out["forward_tflops_mma_sync"] = flops / (fwd / 1e3) / 1e12
+        # the rest runs on the engine the network is created with
+        dns.dns_net_set_engine(net, default_engine)
+        out["engine"] = {0: "mma_sync", 1: "tcgen05", 2: "tcgen05_slab"}[default_engine]
+        fwd = {0: fwd, 1: fwd_tc, 2: fwd_slab}[default_engine]
         out["forward_ms"] = fwd
         out["forward_tflops"] = flops / (fwd / 1e3) / 1e12
         dns.dns_net_train_step(net, batch, G, T, 1e-4)

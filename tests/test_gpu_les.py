@@ -83,7 +83,11 @@ def sample16(dns):
     return g / g.std(), tau / tau.std()
 
 
-@pytest.mark.parametrize("engine", [0, 1], ids=["mma_sync", "tcgen05"])
+ENGINES = [0, 1, 2]
+ENGINE_IDS = ["mma_sync", "tcgen05", "tcgen05_slab"]
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_net_forward_matches_oracle(dns, orc, sample16, engine):
     g, _ = sample16
     net = dns.dns_net_create(16, seed=3)
@@ -104,7 +108,7 @@ def test_net_forward_matches_oracle(dns, orc, sample16, engine):
         dns.dns_net_free(net)
 
 
-@pytest.mark.parametrize("engine", [0, 1], ids=["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
 def test_net_gradients_match_oracle(dns, orc, sample16, engine):
     g, t = sample16
     net = dns.dns_net_create(16, seed=4)
@@ -117,6 +121,60 @@ def test_net_gradients_match_oracle(dns, orc, sample16, engine):
         dns.dns_net_set_params(net, pb)
         loss, grad = dns.dns_net_gradients(net, g, t)
         _, loss_ref, grads_ref = orc.net(bf16(g.cpu().numpy()), split(pb), t.cpu().numpy(), grads=True)
+        assert abs(loss - loss_ref) < 2e-2 * loss_ref
+        got = split(grad)
+        for k in range(6):
+            assert rel(got[k], grads_ref[k]) < 6e-2, k
+    finally:
+        dns.dns_net_free(net)
+
+
+def _bf16_weights(p):
+    pb = p.copy()
+    for o, s in [(0, 32 * 9 * 27), (32 * 9 * 27 + 32, 32 * 32 * 27), (32 * 9 * 27 + 64 + 32 * 32 * 27, 6 * 32 * 27)]:
+        pb[o:o + s] = bf16(p[o:o + s])
+    return pb
+
+
+@pytest.fixture(scope="module")
+def sample64(dns):
+    """Unit-rms random inputs and targets on the 64^3 LES mesh (the network is
+    a function of its input alone; any field exercises every tap and tile)."""
+    gen = torch.Generator(device="cuda").manual_seed(64)
+    return (torch.randn((9, 64, 64, 64), device="cuda", generator=gen),
+            torch.randn((6, 64, 64, 64), device="cuda", generator=gen))
+
+
+@pytest.fixture(scope="module")
+def ref64(dns, orc, sample64):
+    """BF16-rounded initial weights of a 64^3 network (seed 5) and the FP64
+    oracle's output, loss and gradients for them (one oracle run, ~25 s on
+    16 cores, shared by the engines)."""
+    g, t = sample64
+    net = dns.dns_net_create(64, seed=5)
+    try:
+        pb = _bf16_weights(dns.dns_net_get_params(net))
+    finally:
+        dns.dns_net_free(net)
+    out_ref, loss_ref, grads_ref = orc.net(bf16(g.cpu().numpy()), split(pb), t.cpu().numpy(), grads=True)
+    return pb, out_ref, loss_ref, grads_ref
+
+
+@pytest.mark.parametrize("engine", ENGINES, ids=ENGINE_IDS)
+def test_net_forward_and_gradients_at_64_match_oracle(dns, sample64, ref64, engine):
+    # the 64^3 LES mesh of the learned closure: forward output and the
+    # gradient of every parameter block against the FP64 oracle network run
+    # on the same BF16-rounded weights and inputs
+    g, t = sample64
+    pb, out_ref, loss_ref, grads_ref = ref64
+    net = dns.dns_net_create(64, seed=5)
+    try:
+        dns.dns_net_set_engine(net, engine)
+        dns.dns_net_set_params(net, pb)
+        tau = torch.empty((6, 64, 64, 64), device="cuda")
+        dns.dns_net_forward(net, g, tau)
+        loss, grad = dns.dns_net_gradients(net, g, t)
+        assert rel(tau.cpu().numpy(), out_ref) < 2e-2
         assert abs(loss - loss_ref) < 2e-2 * loss_ref
         got = split(grad)
         for k in range(6):
@@ -274,7 +332,7 @@ def test_conv_engines_agree(dns, n):
     gen = torch.Generator(device="cuda").manual_seed(11)
     g = torch.randn((9, n, n, n), device="cuda", generator=gen)
     outs = []
-    for engine in (0, 1):
+    for engine in ENGINES:
         net = dns.dns_net_create(n, seed=12)
         try:
             dns.dns_net_set_engine(net, engine)
@@ -284,10 +342,11 @@ def test_conv_engines_agree(dns, n):
         finally:
             dns.dns_net_free(net)
     assert rel(outs[1], outs[0]) < 1e-2
+    assert rel(outs[2], outs[0]) < 1e-2
     with pytest.raises(dns.DnsError):
         net = dns.dns_net_create(16, seed=1)
         try:
-            dns.dns_net_set_engine(net, 2)
+            dns.dns_net_set_engine(net, 3)
         finally:
             dns.dns_net_free(net)
 
