@@ -255,16 +255,17 @@ int dns_net_free(dns_net net);
  * w2[32][32][27], b2[32], w3[6][32][27], b3[6]. */
 long dns_net_param_count(void);
 /* Convolution engine of the network's layers (forward and input
- * gradients): DNS_CONV_MMA_SYNC (default) runs warp-level BF16 MMAs with
- * the weights staged in shared memory; DNS_CONV_TCGEN05 runs the
+ * gradients): DNS_CONV_MMA_SYNC runs warp-level BF16 MMAs with the weights
+ * staged in shared memory; DNS_CONV_TCGEN05 runs the
  * fifth-generation tensor cores (accumulators in tensor memory, operands
  * in shared memory, one thread issuing the MMAs of a 128-voxel tile, the
  * shifted activations of each of the 27 taps gathered in turn);
  * DNS_CONV_TCGEN05_SLAB runs them from a shared-memory halo slab of a few
  * z lines, every tap's operand a shifted view of the slab, so all 27 taps'
  * MMAs of a tile issue back to back (persistent blocks, next slab copied
- * while the current one's MMAs run).  All compute the same layers (BF16
- * operands, FP32 accumulation).  DNS_ERR_ARG for any other value. */
+ * while the current one's MMAs run; the default, the fastest of the three
+ * at the 64^3 LES mesh).  All compute the same layers (BF16 operands, FP32
+ * accumulation).  DNS_ERR_ARG for any other value. */
 enum dns_conv_engine { DNS_CONV_MMA_SYNC = 0, DNS_CONV_TCGEN05 = 1, DNS_CONV_TCGEN05_SLAB = 2 };
 int dns_net_set_engine(dns_net net, int engine);
 int dns_net_get_engine(dns_net net, int *engine);

@@ -399,13 +399,20 @@ template <int CIN, int COUT, int EPI> static cudaError_t conv_tc_attr() {
 // with no gather or barrier between them.  The layer's weights (27 CIN/16
 // tiles of COUT x 16) stay in shared memory for the whole block.
 //
-// Roles: warp 0 issues the MMAs (one thread), warps 1..8 copy slabs and run
-// the epilogue (two groups of four warps, each covering the 128 tensor-
-// memory lanes, take alternate tiles).  Hand-offs are mbarriers:
+// Roles: warp 0 issues the MMAs (one thread), warps 1..4 copy slabs, warps
+// 5..12 run the epilogue (two groups, each covering the four quadrants of the
+// 128 tensor-memory lanes, taking alternate (tile, 16-channel) units), so the
+// copies of item j + 1, the MMAs of item j and the epilogue of item j - 1
+// overlap.  The epilogue reads 16 accumulator columns of its 32 rows at a
+// time and passes them through a per-warp shared-memory stage, so global
+// stores (and the loads of the forward pre-activations a gradient layer
+// needs) move whole 16-byte pieces of consecutive voxels rather than one
+// 8-byte piece per voxel and lane.
+// Hand-offs are mbarriers:
 //   slab_full[b]  copy warps -> MMA warp: slab buffer b has landed
-//   mma_done[a]   MMA commit -> copy warps: the item's MMAs are complete
-//                 (its slab buffer is free, accumulator a is readable)
-//   acc_free[a]   copy warps -> MMA warp: accumulator a has been read
+//   mma_done[a]   MMA commit -> copy warps: the item's slab buffer is free;
+//                 -> epilogue warps: accumulator a is readable
+//   acc_free[a]   epilogue warps -> MMA warp: accumulator a has been read
 // Two slab buffers (one where two do not fit) and two accumulators let the
 // copies of the next item and the epilogue of the previous one run while
 // the current item's MMAs execute.  Every wait is bounded; on expiry the
@@ -423,6 +430,12 @@ template <int CIN, int COUT> struct ConvSlab {
     static constexpr int BT = COUT / 8 * 256;   // bytes of one B tile (COUT x 16)
     static constexpr int BBYTES = 27 * KS * BT; // all weights
     static constexpr int ACC_COLS = 128;        // tensor-memory columns per accumulator buffer
+    // epilogue staging per warp: 32 rows x 16 channels of FP32 (rows of 20),
+    // reused for the same rows in BF16 (rows of 24), so results leave in
+    // 16-byte pieces
+    static constexpr int ZLD = 20, ALD = 24;
+    static constexpr int STAGE_WARP = 32 * ZLD * 4;
+    static constexpr int STAGE_BYTES = 8 * STAGE_WARP;  // eight epilogue warps
     static SlabGeom geom(int n) {
         SlabGeom g{};
         g.n = n;
@@ -431,18 +444,19 @@ template <int CIN, int COUT> struct ConvSlab {
         g.rows = 3 * (g.Y + 2) * (n + 2) + 2;  // + one padding row at each end
         g.tiles = (g.Y * (n + 2) + 127) / 128;
         g.slab_bytes = (size_t)CH * g.rows * 16;
-        const size_t fixed = (size_t)BBYTES + 1024;
+        const size_t fixed = (size_t)BBYTES + STAGE_BYTES;
         g.nbuf = fixed + 2 * g.slab_bytes <= kMaxSmemLes ? 2 : 1;
         // at least 80 KB, so no more than two blocks share an SM: each holds
         // 256 of the SM's 512 tensor-memory columns
-        g.smem = (size_t)BBYTES + g.nbuf * g.slab_bytes;
+        g.smem = fixed + g.nbuf * g.slab_bytes;
         if (g.smem < 80 * 1024) g.smem = 80 * 1024;
         return g;
     }
 };
 
-constexpr int kSlabCopyWarps = 8;                     // copy + epilogue warps (1..8)
-constexpr int kSlabThreads = 32 * (1 + kSlabCopyWarps);  // + the MMA warp (0)
+constexpr int kSlabCopyWarps = 4;  // warps 1..4 land the slabs
+constexpr int kSlabEpiWarps = 8;   // warps 5..12 read the accumulators (two per tensor-memory lane quadrant)
+constexpr int kSlabThreads = 32 * (1 + kSlabCopyWarps + kSlabEpiWarps);  // + the MMA warp (0)
 
 // Bounded mbarrier wait; on expiry marks the block failed (shared flag) and
 // records the timeout.  Returns false if the block has failed.
@@ -467,7 +481,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, cons
     typedef ConvSlab<CIN, COUT> C;
     constexpr uint32_t IDESC = tc::idesc_bf16_f32(128, COUT);
     constexpr uint32_t TCOLS = 2 * C::ACC_COLS;
-    constexpr int NCOPY = 32 * kSlabCopyWarps;
+    constexpr int NCOPY = 32 * kSlabCopyWarps, NEPI = 32 * kSlabEpiWarps;
     static_assert(COUT == 16 || COUT == 32, "one or two 16-column accumulator loads");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char *sB = smem_raw;
@@ -489,7 +503,7 @@ __global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, cons
         for (int i = 0; i < 2; ++i) {
             mbar_init(&slab_full[i], NCOPY);
             mbar_init(&mma_done[i], 1);
-            mbar_init(&acc_free[i], NCOPY);
+            mbar_init(&acc_free[i], NEPI);
         }
         s_ok = 1;
     }
@@ -518,14 +532,19 @@ __global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, cons
                 const uint64_t adesc0 = (uint64_t)((a0 & 0x3FFFFu) >> 4) | ((uint64_t)(lbo16 & 0x3FFFu) << 16) |
                                         ((uint64_t)(128 >> 4) << 32) | (1ull << 46);
                 const uint32_t tacc = tmem_base + (uint32_t)((j & 1) * C::ACC_COLS);
+                // tile by tile, all 27 taps' MMAs back to back (a single thread's
+                // descriptor arithmetic stays in registers: a runtime-indexed
+                // array here would be reloaded from local memory after every
+                // MMA, whose asm is a compiler memory barrier)
                 for (int t = 0; t < sg.tiles; ++t) {
                     const int p0 = min(128 * t, npos - 128);
 #pragma unroll
                     for (int tap = 0; tap < 27; ++tap) {
                         const int dx = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dz = tap % 3 - 1;
-                        // slab row of output p0 for this tap, in 16-byte units (-1 for the
-                        // first tap of the first tile: the front padding row); signed, so
-                        // the sum with the descriptor's address field never borrows
+                        // slab row of output p0 for this tap, in 16-byte units (-1 for
+                        // the first tap of the first tile: the front padding row);
+                        // signed, so the sum with the descriptor's address field
+                        // never borrows
                         const int row = p0 + dz + (1 + dx) * plane + (1 + dy) * L;
 #pragma unroll
                         for (int kk = 0; kk < C::KS; ++kk) {
@@ -542,12 +561,16 @@ __global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, cons
                 mbar_wait_bounded(&mma_done[committed & 1], (uint32_t)((committed >> 1) & 1));
         }
         __syncwarp();
-    } else {
-        // ---------------- copy + epilogue warps
-        const int cw = warp - 1;         // 0..7
-        const int wq = warp & 3;         // tensor-memory lane quadrant this warp may read
-        const int grp = cw >> 2;         // tiles t = grp, grp + 2, ...
-        auto gather = [&](long long w, int b) {
+    } else if (warp <= kSlabCopyWarps) {
+        // ---------------- copy warps: one slab line per warp at a time; its n
+        // voxels are contiguous in X, lane e copies chunk e mod CH of row
+        // e / CH (the halo rows r = 0 and r = n + 1 wrap to z = n - 1, 0)
+        const int cw = warp - 1;
+        for (int j = 0; j < nitems; ++j) {
+            const int b = nbuf == 2 ? (j & 1) : 0;
+            const int jb = j - nbuf;  // the buffer was last read by the MMAs of item jb
+            if (jb >= 0 && !slab_wait(&mma_done[jb & 1], (uint32_t)((jb >> 1) & 1), &s_ok, err)) break;
+            const long long w = first + (long long)j * stride;
             const int x = (int)(w / ybl), y0 = (int)(w % ybl) * Y;
             unsigned char *dst = sSlab + (size_t)b * sg.slab_bytes;
             const int nlines = 3 * (Y + 2);
@@ -563,61 +586,103 @@ __global__ void __launch_bounds__(kSlabThreads, 1) k_conv_slab(SlabGeom sg, cons
                 }
             }
             cp_async_commit();
-        };
-        auto epilogue = [&](long long w, int j) {
-            const int x = (int)(w / ybl), y0 = (int)(w % ybl) * Y;
-            const uint32_t tacc = tmem_base + (uint32_t)((j & 1) * C::ACC_COLS) + ((uint32_t)(32 * wq) << 16);
-            const int npos = Y * L;
-            for (int t = grp; t < sg.tiles; t += 2) {
-                const int p0 = min(128 * t, npos - 128);
-                const int p = p0 + 32 * wq + lane;
-                float acc[COUT];
-                tc::ld16(tacc + t * COUT, *reinterpret_cast<float(*)[16]>(acc));
-                if constexpr (COUT == 32) tc::ld16(tacc + t * COUT + 16, *reinterpret_cast<float(*)[16]>(acc + 16));
-                const int yl = p / L, z = p % L - 1;
-                if (p < 128 * t || z < 0 || z >= n) continue;  // halo row, or computed by the previous tile
-                const long long v = ((long long)x * n + (y0 + yl)) * n + z;
-#pragma unroll
-                for (int o = 0; o < COUT; o += 2) {
-                    float y0v = acc[o], y1v = acc[o + 1];
-                    if (bias) {
-                        y0v += bias[o];
-                        y1v += bias[o + 1];
-                    }
-                    if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT)
-                        *reinterpret_cast<float2 *>(Z + v * COUT + o) = make_float2(y0v, y1v);
-                    if constexpr (EPI == EPI_HIDDEN)
-                        *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
-                            __floats2bfloat162_rn(gelu_f(y0v), gelu_f(y1v));
-                    if constexpr (EPI == EPI_DGRAD) {
-                        const float2 zp = *reinterpret_cast<const float2 *>(Zp + v * COUT + o);
-                        *reinterpret_cast<__nv_bfloat162 *>(A + v * COUT + o) =
-                            __floats2bfloat162_rn(y0v * gelu_d(zp.x), y1v * gelu_d(zp.y));
-                    }
-                }
-            }
-        };
-        for (int j = 0; j <= nitems; ++j) {
-            if (j < nitems) {
-                const int b = nbuf == 2 ? (j & 1) : 0;
-                // the buffer was last read by the MMAs of item j - nbuf
-                const int jb = j - nbuf;
-                if (jb >= 0 && !slab_wait(&mma_done[jb & 1], (uint32_t)((jb >> 1) & 1), &s_ok, err)) break;
-                gather(first + (long long)j * stride, b);
-                cp_async_wait<0>();
-                fence_proxy_async_smem();
-                mbar_arrive(&slab_full[b]);
-            }
-            if (j >= 1) {
-                const int je = j - 1;
-                if (!slab_wait(&mma_done[je & 1], (uint32_t)((je >> 1) & 1), &s_ok, err)) break;
-                tc::fence_after_sync();
-                epilogue(first + (long long)je * stride, je);
-                tc::fence_before_sync();
-                mbar_arrive(&acc_free[je & 1]);
-            }
+            cp_async_wait<0>();
+            fence_proxy_async_smem();
+            mbar_arrive(&slab_full[b]);
         }
         cp_async_wait<0>();
+    } else {
+        // ---------------- epilogue warps
+        const int ew = warp - 1 - kSlabCopyWarps;  // 0..7
+        const int wq = warp & 3;                   // tensor-memory lane quadrant this warp may read
+        const int grp = ew >> 2;                   // units u = grp, grp + 2, ...
+        float *zst = reinterpret_cast<float *>(sSlab + (size_t)nbuf * sg.slab_bytes + (size_t)ew * C::STAGE_WARP);
+        __nv_bfloat16 *ast = reinterpret_cast<__nv_bfloat16 *>(zst);  // the same rows, later, in BF16
+        const int npos = Y * L;
+        constexpr int HALVES = COUT / 16;
+        for (int j = 0; j < nitems; ++j) {
+            if (!slab_wait(&mma_done[j & 1], (uint32_t)((j >> 1) & 1), &s_ok, err)) break;
+            tc::fence_after_sync();
+            const long long w = first + (long long)j * stride;
+            const int x = (int)(w / ybl), y0 = (int)(w % ybl) * Y;
+            const uint32_t tacc = tmem_base + (uint32_t)((j & 1) * C::ACC_COLS) + ((uint32_t)(32 * wq) << 16);
+            for (int u = grp; u < sg.tiles * HALVES; u += 2) {
+                const int t = u / HALVES, h = u % HALVES;
+                const int p0 = min(128 * t, npos - 128);
+                // this lane's row: its voxel, or -1 (halo row, or a row the
+                // previous tile already produced); other rows' by shuffle
+                long long vme;
+                {
+                    const int p = p0 + 32 * wq + lane;
+                    const int yl = p / L, z = p % L - 1;
+                    vme = (p < 128 * t || z < 0 || z >= n) ? -1 : ((long long)x * n + (y0 + yl)) * n + z;
+                }
+                float acc[16];
+                tc::ld16(tacc + t * COUT + 16 * h, acc);
+                float zp[16];
+                if constexpr (EPI == EPI_DGRAD) {
+                    // forward pre-activations of these rows and channels, staged
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = lane + 32 * k, r = e >> 2, q = e & 3;
+                        const long long v = __shfl_sync(0xffffffffu, vme, r);
+                        float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+                        if (v >= 0) z4 = *reinterpret_cast<const float4 *>(Zp + v * COUT + 16 * h + 4 * q);
+                        *reinterpret_cast<float4 *>(zst + r * C::ZLD + 4 * q) = z4;
+                    }
+                    __syncwarp();
+#pragma unroll
+                    for (int o = 0; o < 16; ++o) zp[o] = zst[lane * C::ZLD + o];
+                    __syncwarp();
+                }
+                float yv[16];
+#pragma unroll
+                for (int o = 0; o < 16; ++o) yv[o] = acc[o] + (bias ? bias[16 * h + o] : 0.f);
+                if constexpr (EPI == EPI_HIDDEN || EPI == EPI_OUT) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        *reinterpret_cast<float4 *>(zst + lane * C::ZLD + 4 * q) =
+                            make_float4(yv[4 * q], yv[4 * q + 1], yv[4 * q + 2], yv[4 * q + 3]);
+                    __syncwarp();
+                    // whole 16-byte pieces out, 4 lanes per row
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int e = lane + 32 * k, r = e >> 2, q = e & 3;
+                        const long long v = __shfl_sync(0xffffffffu, vme, r);
+                        if (v >= 0)
+                            *reinterpret_cast<float4 *>(Z + v * COUT + 16 * h + 4 * q) =
+                                *reinterpret_cast<const float4 *>(zst + r * C::ZLD + 4 * q);
+                    }
+                    __syncwarp();
+                }
+                if constexpr (EPI == EPI_HIDDEN || EPI == EPI_DGRAD) {
+                    __nv_bfloat162 a2[8];
+#pragma unroll
+                    for (int o = 0; o < 16; o += 2) {
+                        if constexpr (EPI == EPI_HIDDEN)
+                            a2[o / 2] = __floats2bfloat162_rn(gelu_f(yv[o]), gelu_f(yv[o + 1]));
+                        else
+                            a2[o / 2] = __floats2bfloat162_rn(yv[o] * gelu_d(zp[o]), yv[o + 1] * gelu_d(zp[o + 1]));
+                    }
+                    uint4 *ad = reinterpret_cast<uint4 *>(ast + lane * C::ALD);
+                    ad[0] = *reinterpret_cast<const uint4 *>(&a2[0]);
+                    ad[1] = *reinterpret_cast<const uint4 *>(&a2[4]);
+                    __syncwarp();
+                    // whole 16-byte pieces out, 2 lanes per row
+#pragma unroll
+                    for (int k = 0; k < 2; ++k) {
+                        const int e = lane + 32 * k, r = e >> 1, q = e & 1;
+                        const long long v = __shfl_sync(0xffffffffu, vme, r);
+                        if (v >= 0)
+                            *reinterpret_cast<uint4 *>(A + v * COUT + 16 * h + 8 * q) =
+                                *reinterpret_cast<const uint4 *>(ast + r * C::ALD + 8 * q);
+                    }
+                    __syncwarp();
+                }
+            }
+            tc::fence_before_sync();
+            mbar_arrive(&acc_free[j & 1]);
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -851,7 +916,7 @@ struct dns_net_ctx {
     __nv_bfloat16 *W1 = nullptr, *W2 = nullptr, *W3 = nullptr, *W2f = nullptr, *W3f = nullptr;
     __nv_bfloat16 *W1c = nullptr, *W2c = nullptr, *W3c = nullptr, *W2fc = nullptr, *W3fc = nullptr;
     int *err = nullptr;  // device status word of the convolutions' bounded waits
-    int engine = 0;      // convolution engine: DNS_CONV_MMA_SYNC or DNS_CONV_TCGEN05
+    int engine = DNS_CONV_TCGEN05_SLAB;  // convolution engine (dns_conv_engine); the fastest is the default
     // activations for one sample
     __nv_bfloat16 *X0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY3 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Y3 = nullptr, *wpart = nullptr;
