@@ -64,8 +64,11 @@ enum dns_status {
     DNS_ERR_UNSUPPORTED = 6  /* N, dtype or option not supported */
 };
 
-/* Create a solver for an N^3 box.  N: even, 8 <= N <= 1024, N = 2^a or
- * 3 * 2^a (else DNS_ERR_UNSUPPORTED).  nu > 0 viscosity, dt > 0 time step.
+/* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 8, 12,
+ * 16, 24, 32, 36, 48, 64, 72, 96, 128, 144, 192, 256, 288, 384, 512, 576,
+ * 768, 1024, i.e. the multiples of 4 from 8 to 1024 whose odd part is 1, 3
+ * or 9 (transform stages of radix 3 and powers of two); any other N is
+ * DNS_ERR_UNSUPPORTED.  nu > 0 viscosity, dt > 0 time step.
  * cuda_stream: a cudaStream_t to run on, or NULL for a stream the handle
  * creates.  The velocity starts at zero, t = 0, step = 0.
  * Errors: DNS_ERR_ARG, DNS_ERR_UNSUPPORTED, DNS_ERR_OOM, DNS_ERR_CUDA. */

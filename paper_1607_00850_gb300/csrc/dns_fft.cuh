@@ -56,11 +56,10 @@ template <int SIGN, typename T> __device__ __forceinline__ T cmul_si(T a) {
 template <typename T, typename S> __device__ __forceinline__ T cscale(T a, S s) { a.x *= s; a.y *= s; return a; }
 
 // ---------------------------------------------------------------------------
-// Radix plan: N = 3^b * 2^a (b <= 1).  A radix-3 stage first, then the power
-// of two split into the fewest stages whose radices are at most MAXR (8, 16
-// or 32), as equal as possible, smaller first: 2^9 with MAXR 8 -> 8*8*8,
-// with 32 -> 16*32;
-// 2^10 with 8 -> 4*4*8*8.
+// Radix plan: N = 3^b * 2^a.  b radix-3 stages first, then the power of two
+// split into the fewest stages whose radices are at most MAXR (8, 16 or
+// 32), as equal as possible, smaller first: 2^9 with MAXR 8 -> 8*8*8, with
+// 32 -> 16*32; 2^10 with 8 -> 4*4*8*8; 9 * 2^5 with 8 -> 3*3*4*8.
 struct FftPlan {
     int nst;
     int r[8];
@@ -70,7 +69,7 @@ struct FftPlan {
 __host__ __device__ constexpr FftPlan make_plan(int N, int MAXR = 8) {
     FftPlan p{0, {0, 0, 0, 0, 0, 0, 0, 0}, {0, 0, 0, 0, 0, 0, 0, 0}};
     int n = N;
-    if (n % 3 == 0) { p.r[p.nst++] = 3; n /= 3; }
+    while (n % 3 == 0) { p.r[p.nst++] = 3; n /= 3; }
     int a = 0;
     while ((1 << a) < n) ++a;
     int lmax = MAXR >= 32 ? 5 : (MAXR >= 16 ? 4 : 3);

@@ -49,7 +49,8 @@ def test_binding_covers_every_declared_symbol():
 
 def test_init_validates_arguments_before_device_work(lib):
     h = ctypes.c_void_p()
-    assert lib.dns_init(10, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6   # N not 2^a or 3*2^a
+    assert lib.dns_init(10, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6   # N not 2^a 3^b
+    assert lib.dns_init(40, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
     assert lib.dns_init(2048, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
     assert lib.dns_init(7, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
     assert lib.dns_init(32, 0.01, 0.01, 3, None, ctypes.byref(h)) == 1   # dtype
@@ -79,8 +80,10 @@ def test_supported_sizes_match_plan():
     from paper_1607_00850_gb300 import build, dns
     assert tuple(build.SIZES) == tuple(dns.SUPPORTED_N)
     for n in dns.SUPPORTED_N:
-        m = n // 3 if n % 3 == 0 else n
-        assert m & (m - 1) == 0 and n % 2 == 0
+        m = n
+        while m % 3 == 0:
+            m //= 3
+        assert m & (m - 1) == 0 and n % 4 == 0
 
 
 class _FakeDeviceTensor:

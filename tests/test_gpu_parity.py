@@ -46,7 +46,7 @@ def kept_mask(N):
 
 
 # ---------------------------------------------------------------- right-hand side
-@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 48, 64, 96])
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 36, 48, 64, 72, 96])
 @pytest.mark.parametrize("dtype", DTYPES, ids=DNAME.get)
 def test_rhs_matches_oracle(dns, orc, N, dtype):
     nu = 0.013
