@@ -61,7 +61,8 @@ enum dns_status {
     DNS_ERR_CUDA = 3,        /* a CUDA runtime call or kernel launch failed */
     DNS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
     DNS_ERR_NONFINITE = 5,   /* NaN or Inf found in the state */
-    DNS_ERR_UNSUPPORTED = 6  /* N, dtype or option not supported */
+    DNS_ERR_UNSUPPORTED = 6, /* N, dtype or option not supported */
+    DNS_ERR_GUARD = 7        /* a guard region around a device buffer was overwritten */
 };
 
 /* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 8, 12,
@@ -151,6 +152,15 @@ int dns_set_integrator(dns_handle h, int kind);
  * state is then not trustworthy and the status stays set). */
 int dns_synchronize(dns_handle h);
 
+/* Stray-write check (the paper has no counterpart; a memory checker is not
+ * available on every system): every device buffer a handle allocates sits
+ * between two 256-byte guard regions filled with a fixed byte pattern.  This
+ * call drains the handle's streams, reads every guard region back and
+ * returns DNS_ERR_GUARD if any byte changed, i.e. if some kernel wrote past
+ * either end of a buffer; DNS_OK otherwise (DNS_ERR_CUDA on a copy error).
+ * Synchronising; the buffers themselves are untouched. */
+int dns_check_guards(dns_handle h);
+
 /* Check of the failure detection above: queue on the handle's stream a
  * one-block kernel whose bounded wait (on an mbarrier nothing completes)
  * gives up after `seconds` (0 < seconds <= 2, else DNS_ERR_ARG), so that the
@@ -217,6 +227,8 @@ typedef struct dns_ens_ctx *dns_ensemble;
 int dns_ensemble_init(int nbox, const int *N, const double *nu, double dt, int dtype, void *cuda_stream,
                       dns_ensemble *out);
 int dns_ensemble_free(dns_ensemble e);
+/* dns_check_guards for every context of an ensemble. */
+int dns_ensemble_check_guards(dns_ensemble e);
 /* Set / read box b (0 <= b < nbox); synchronising like the single-box calls. */
 int dns_ensemble_set_velocity(dns_ensemble e, int box, const void *uhat, int on_device);
 int dns_ensemble_get_velocity(dns_ensemble e, int box, void *uhat, int on_device);

@@ -34,6 +34,16 @@ static PassGetter getter_for(int N) {
 
 using dns::Geo;
 
+// Every device buffer of a handle sits between two guard regions of
+// kGuardBytes filled with kGuardByte; dns_check_guards reads them back, so a
+// kernel that writes past either end of a buffer is caught.
+constexpr size_t kGuardBytes = 256;  // keeps the buffer itself 256-byte aligned
+constexpr unsigned char kGuardByte = 0xA5;
+struct GuardedAlloc {
+    void *base, *user;
+    size_t bytes;
+};
+
 struct dns_ctx {
     int N = 0, dtype = 0;
     double nu = 0, dt = 0, t = 0;
@@ -55,6 +65,7 @@ struct dns_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     long long bytes = 0;
+    std::vector<GuardedAlloc> allocs;  // every device buffer, with its guard regions
     int plan[5] = {0, 0, 0, 0, 0};  // variant of P1, P2, P3, P4, P5a
     int integrator = 0;             // DNS_RK4 or DNS_IFRK4
     dns::LesClosure *closure = nullptr;  // learned subgrid closure (LES handles), or nullptr
@@ -91,25 +102,61 @@ static void release(dns_ctx *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
     if (h->graph) cudaGraphDestroy(h->graph);
-    void *bufs[] = {h->U, h->U0, h->U1, h->A, h->B, h->io, h->rin, h->rout, h->tw, h->partials, h->sums, h->Ek,
-                    h->nu_box, h->Om, h->rom, h->err};
-    for (void *p : bufs)
-        if (p) cudaFree(p);
     if (h->host) cudaFreeHost(h->host);
     if (h->closure) dns::les_closure_release(h->closure);
-    if (h->Fext) cudaFree(h->Fext);
     drop_async_io(h);
+    for (const GuardedAlloc &a : h->allocs) cudaFree(a.base);
+    h->allocs.clear();
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
 
 static int dev_alloc(dns_ctx *h, void **p, size_t bytes) {
-    if (cudaMalloc(p, bytes) != cudaSuccess) {
-        *p = nullptr;
+    void *base = nullptr;
+    *p = nullptr;
+    if (cudaMalloc(&base, bytes + 2 * kGuardBytes) != cudaSuccess) {
         cudaGetLastError();
         return DNS_ERR_OOM;
     }
+    char *user = static_cast<char *>(base) + kGuardBytes;
+    cudaError_t e = cudaMemset(base, kGuardByte, kGuardBytes);
+    if (e == cudaSuccess) e = cudaMemset(user + bytes, kGuardByte, kGuardBytes);
+    if (e != cudaSuccess) {
+        g_last_cuda = e;
+        cudaFree(base);
+        return DNS_ERR_CUDA;
+    }
+    h->allocs.push_back({base, user, bytes});
     h->bytes += (long long)bytes;
+    *p = user;
+    return DNS_OK;
+}
+
+static void dev_free(dns_ctx *h, void *p) {
+    for (size_t i = 0; i < h->allocs.size(); ++i)
+        if (h->allocs[i].user == p) {
+            cudaFree(h->allocs[i].base);
+            h->bytes -= (long long)h->allocs[i].bytes;
+            h->allocs.erase(h->allocs.begin() + (long)i);
+            return;
+        }
+}
+
+// DNS_OK if every guard region of every buffer still holds kGuardByte,
+// DNS_ERR_GUARD if one was overwritten (call after the work has drained).
+static int check_guards(dns_ctx *h) {
+    std::vector<unsigned char> buf(kGuardBytes);
+    for (const GuardedAlloc &a : h->allocs)
+        for (int side = 0; side < 2; ++side) {
+            const char *src = side == 0 ? static_cast<const char *>(a.base) : static_cast<const char *>(a.user) + a.bytes;
+            cudaError_t e = cudaMemcpy(buf.data(), src, kGuardBytes, cudaMemcpyDeviceToHost);
+            if (e != cudaSuccess) {
+                g_last_cuda = e;
+                return DNS_ERR_CUDA;
+            }
+            for (unsigned char b : buf)
+                if (b != kGuardByte) return DNS_ERR_GUARD;
+        }
     return DNS_OK;
 }
 
@@ -425,6 +472,7 @@ const char *dns_strerror(int status) {
         case DNS_ERR_TIMEOUT: return "bounded device wait timed out";
         case DNS_ERR_NONFINITE: return "non-finite value in the state";
         case DNS_ERR_UNSUPPORTED: return "unsupported size, dtype or option";
+        case DNS_ERR_GUARD: return "a guard region around a device buffer was overwritten";
         default: return "unknown status";
     }
 }
@@ -442,6 +490,13 @@ int dns_free(dns_handle h) {
     cudaStreamSynchronize(h->stream);
     release(h);
     return DNS_OK;
+}
+
+int dns_check_guards(dns_handle h) {
+    if (!h) return DNS_ERR_ARG;
+    for (cudaStream_t st : {h->stream, h->s_in, h->s_out})
+        if (st && cudaStreamSynchronize(st) != cudaSuccess) return DNS_ERR_CUDA;
+    return check_guards(h);
 }
 
 // After the stream has drained: DNS_ERR_TIMEOUT if a kernel gave up a
@@ -497,11 +552,9 @@ static void drop_async_io(dns_ctx *h) {
             cudaEventDestroy(*ev);
             *ev = nullptr;
         }
-    const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
     for (void **p : {&h->io_in, &h->io_out[0], &h->io_out[1]})
         if (*p) {
-            cudaFree(*p);
-            h->bytes -= (long long)bytes;
+            dev_free(h, *p);
             *p = nullptr;
         }
 }
@@ -1075,6 +1128,16 @@ int dns_ensemble_free(dns_ensemble e) {
     return DNS_OK;
 }
 
+int dns_ensemble_check_guards(dns_ensemble e) {
+    if (!e) return DNS_ERR_ARG;
+    if (cudaStreamSynchronize(e->stream) != cudaSuccess) return DNS_ERR_CUDA;
+    for (dns_ctx *c : e->cls) {
+        const int rc = dns_check_guards(c);
+        if (rc != DNS_OK) return rc;
+    }
+    return DNS_OK;
+}
+
 int dns_ensemble_set_velocity(dns_ensemble e, int box, const void *uhat, int on_device) {
     if (!e || !uhat || box < 0 || box >= e->nbox) return DNS_ERR_ARG;
     return set_state(e->cls[e->box_cls[box]], e->box_idx[box], uhat, on_device);
@@ -1181,11 +1244,12 @@ int internal_set_closure(dns_handle h, LesClosure *c) {
     if (h->closure) les_closure_release(h->closure);
     h->closure = c;
     if (c && !h->Fext) {
-        if (cudaMalloc(&h->Fext, 3 * h->g.sS * h->creal) != cudaSuccess) {
+        const int rc = dev_alloc(h, &h->Fext, 3 * h->g.sS * h->creal);
+        if (rc != DNS_OK) {
             h->Fext = nullptr;
             h->closure = nullptr;
             les_closure_release(c);
-            return DNS_ERR_OOM;
+            return rc;
         }
     }
     if (h->exec) cudaGraphExecDestroy(h->exec);

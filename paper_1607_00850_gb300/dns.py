@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libdns.so")
 DNS_F32, DNS_F64, DNS_F32_ACC64 = 0, 1, 2
 DTYPE_NAMES = {"f32": DNS_F32, "f64": DNS_F64, "f32_acc64": DNS_F32_ACC64}
 STATUS = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_OOM", 3: "DNS_ERR_CUDA", 4: "DNS_ERR_TIMEOUT",
-          5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED"}
+          5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED", 7: "DNS_ERR_GUARD"}
 SUPPORTED_N = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 128, 144, 192, 256, 288, 384, 512, 576, 768, 1024)
 
 # symbol -> (restype, argtypes); the complete exported surface of dns.h
@@ -37,6 +37,8 @@ SIGNATURES = {
     "dns_step": (_i, [_vp, _i]),
     "dns_step_profiled": (_i, [_vp, _i, _dp, _dp]),
     "dns_synchronize": (_i, [_vp]),
+    "dns_check_guards": (_i, [_vp]),
+    "dns_ensemble_check_guards": (_i, [_vp]),
     "dns_check_wait_timeout": (_i, [_vp, _d]),
     "dns_energy": (_i, [_vp, _dp]),
     "dns_dissipation": (_i, [_vp, _dp]),
@@ -198,6 +200,16 @@ def dns_step_profiled(h: int, n: int):
 
 def dns_synchronize(h: int) -> None:
     _check(load().dns_synchronize(h), "dns_synchronize")
+
+
+def dns_check_guards(h: int) -> None:
+    """Raise DnsError (DNS_ERR_GUARD) if a kernel wrote past either end of
+    one of the handle's device buffers."""
+    _check(load().dns_check_guards(h), "dns_check_guards")
+
+
+def dns_ensemble_check_guards(e: int) -> None:
+    _check(load().dns_ensemble_check_guards(e), "dns_ensemble_check_guards")
 
 
 def dns_check_wait_timeout(h: int, seconds: float) -> None:
@@ -395,10 +407,14 @@ class Solver:
         self._pending = []  # host buffers of queued asynchronous I/O, held until synchronize()
         self.h = dns_init(N, nu, dt, dtype, stream)
 
-    def close(self):
+    def close(self, check_guards: bool = True):
+        """Free the handle; first (by default) verify that no kernel wrote
+        past the ends of its device buffers (DnsError DNS_ERR_GUARD)."""
         if self.h:
-            dns_free(self.h)
-            self.h = None
+            h, self.h = self.h, None
+            rc = load().dns_check_guards(h) if check_guards else 0
+            dns_free(h)
+            _check(rc, "dns_check_guards")
 
     def __enter__(self):
         return self
@@ -408,7 +424,7 @@ class Solver:
 
     def __del__(self):
         try:
-            self.close()
+            self.close(check_guards=False)
         except Exception:
             pass
 
@@ -488,10 +504,12 @@ class Ensemble:
         self.Ns, self.nus, self.dt, self.dtype = [int(n) for n in Ns], [float(v) for v in nus], float(dt), int(dtype)
         self.h = dns_ensemble_init(self.Ns, self.nus, dt, dtype, stream)
 
-    def close(self):
+    def close(self, check_guards: bool = True):
         if self.h:
-            dns_ensemble_free(self.h)
-            self.h = None
+            h, self.h = self.h, None
+            rc = load().dns_ensemble_check_guards(h) if check_guards else 0
+            dns_ensemble_free(h)
+            _check(rc, "dns_ensemble_check_guards")
 
     def __enter__(self):
         return self
@@ -501,7 +519,7 @@ class Ensemble:
 
     def __del__(self):
         try:
-            self.close()
+            self.close(check_guards=False)
         except Exception:
             pass
 

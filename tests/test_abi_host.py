@@ -67,12 +67,14 @@ def test_null_handle_is_rejected(lib):
     assert lib.dns_energy(None, None) == 1
     assert lib.dns_set_velocity(None, None, 0) == 1
     assert lib.dns_rhs(None, None, None, 0) == 1
+    assert lib.dns_check_guards(None) == 1
+    assert lib.dns_ensemble_check_guards(None) == 1
 
 
 def test_status_strings(lib):
     from paper_1607_00850_gb300 import dns
-    for code in range(7):
-        assert dns.dns_strerror(code)
+    for code in range(8):
+        assert dns.dns_strerror(code) != "unknown status"
     assert dns.dns_strerror(99) == "unknown status"
 
 
