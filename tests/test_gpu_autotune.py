@@ -37,7 +37,7 @@ def test_every_variant_matches_oracle(dns, orc, N, dtype):
     with dns.Solver(N, nu, 0.001, dtype) as s:
         checked = 0
         for p in range(5):
-            for v in range(16):
+            for v in range(32):
                 if dns.dns_variant_info(s.h, p, v) is None:
                     continue
                 plan = [0] * 5

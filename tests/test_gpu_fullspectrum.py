@@ -117,7 +117,7 @@ def test_every_variant_full_spectrum(dns, box, dtype):
     checked = 0
     with dns.Solver(N, NU, 1e-4, dtype) as s:
         for p in range(5):
-            for v in range(16):
+            for v in range(32):
                 if dns.dns_variant_info(s.h, p, v) is None:
                     continue
                 plan = [0] * 5
