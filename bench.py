@@ -454,18 +454,26 @@ def bf16_peak():
 
 def les_closure_bench():
     """The learned LES closure at 64^3 (9 -> 32 -> 32 -> 6 periodic 3^3
-    convolutions, BF16 tensor-core MMA with FP32 accumulation): forward
-    TFLOP/s against the dense BF16 peak, training step per sample, LES step
+    convolutions, BF16 tensor-core MMA with FP32 accumulation): the
+    convolution layers' TFLOP/s (device time) against the dense BF16 burst
+    peak, the forward per API call, training step per sample, LES step
     costs, next to a 256^3 DNS step."""
     from paper_1607_00850_gb300 import experiments
     r = experiments.les_bench(64)
     peak, src = bf16_peak()
-    engines = {"k_conv (mma_sync)": r["forward_tflops_mma_sync"], "k_conv_tc (tcgen05)": r["forward_tflops_tcgen05"],
-               "k_conv_slab (tcgen05, halo slab)": r["forward_tflops_tcgen05_slab"]}
-    kernel = max(engines, key=engines.get)
-    best = engines[kernel]
+    # the convolution kernels' own device time (CUDA events around each layer
+    # on the network's stream, forwards queued back to back); the per-call
+    # figures (forward_ms_*) add the input conversion, the output unpacking,
+    # a stream synchronisation and the status-word read of dns_net_forward
+    engines = {"k_conv (mma_sync)": "mma_sync", "k_conv_tc (tcgen05)": "tcgen05",
+               "k_conv_slab (tcgen05, halo slab)": "tcgen05_slab"}
+    kernel = max(engines, key=lambda k: r["conv_tflops_" + engines[k]])
+    tag = engines[kernel]
+    best = r["conv_tflops_" + tag]
     r["roofline"] = {"bound": "tensor", "kernel": kernel + ", three layers, fastest engine",
-                     "achieved": best, "peak": peak, "unit": "TFLOP/s", "frac": best / peak, "peak_source": src}
+                     "achieved": best, "peak": peak, "unit": "TFLOP/s", "frac": best / peak, "peak_source": src,
+                     "conv_ms": r["conv_ms_" + tag], "layer_ms": r["conv_layer_ms_" + tag],
+                     "flops_per_forward": r["forward_flops"]}
     return r
 
 

@@ -292,6 +292,15 @@ int dns_net_set_params(dns_net net, const float *host, long count);
 int dns_net_set_closure_scaling(dns_net net, double in_scale, double out_scale);
 /* tau[6][n^3] = network(g[9][n^3]) (device buffers; synchronising). */
 int dns_net_forward(dns_net net, const float *g, float *tau);
+/* reps forwards of dns_net_forward queued back to back on the network's
+ * stream, with CUDA events around each convolution layer and around each
+ * forward (no synchronisation between them): layer_ms[0..2] receives the
+ * mean device time of layers 1, 2 and 3, total_ms the mean time per forward
+ * from the first launch of the first to the last of the last (input
+ * conversion and output unpacking included).  Same arguments as
+ * dns_net_forward otherwise; 1 <= reps <= 10000, else DNS_ERR_ARG.
+ * Synchronising.  No counterpart in the paper (measurement). */
+int dns_net_forward_profiled(dns_net net, const float *g, float *tau, int reps, double *layer_ms, double *total_ms);
 /* Mean squared error loss of one sample and (optional) its gradient with
  * respect to every parameter, in the parameter order above (host buffer). */
 int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count);

@@ -811,12 +811,17 @@ __global__ void k_colsum(const __nv_bfloat16 *__restrict__ d, long long V, int C
 }
 
 // g[9][V] floats -> X0[V][16] BF16 (channels 9..15 zero)
+// One thread per voxel: nine reads, each coalesced along v, and the voxel's
+// 32-byte row written as two 16-byte stores.
 __global__ void k_prep_input(const float *__restrict__ g, long long V, __nv_bfloat16 *__restrict__ X0) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= V * 16) return;
-    const long long v = e / 16;
-    const int c = (int)(e % 16);
-    X0[e] = __float2bfloat16(c < 9 ? g[c * V + v] : 0.f);
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    __align__(16) __nv_bfloat16 row[16];
+#pragma unroll
+    for (int c = 0; c < 16; ++c) row[c] = __float2bfloat16(c < 9 ? g[c * V + v] : 0.f);
+    uint4 *dst = reinterpret_cast<uint4 *>(X0 + v * 16);
+    dst[0] = reinterpret_cast<const uint4 *>(row)[0];
+    dst[1] = reinterpret_cast<const uint4 *>(row)[1];
 }
 
 // The output layer is computed 16 channels wide (the MMA's K granularity for
@@ -856,11 +861,26 @@ __global__ void k_sum_d(const double *p, int n, double scale, double *out) {
 }
 
 // Y[V][OUTP] -> tau[6][V] floats
+// One thread per voxel: the first six channels of its row (one 16-byte and
+// one 8-byte load) to the six planes of tau, each store coalesced along v.
 __global__ void k_out_to_tau(const float *__restrict__ Y, long long V, float *__restrict__ tau, float scale) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e >= 6 * V) return;
-    const int o = (int)(e / V);
-    tau[e] = scale * Y[(e % V) * OUTP + o];
+    const long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const float4 a = *reinterpret_cast<const float4 *>(Y + v * OUTP);
+    const float2 b = *reinterpret_cast<const float2 *>(Y + v * OUTP + 4);
+    tau[v] = scale * a.x;
+    tau[V + v] = scale * a.y;
+    tau[2 * V + v] = scale * a.z;
+    tau[3 * V + v] = scale * a.w;
+    tau[4 * V + v] = scale * b.x;
+    tau[5 * V + v] = scale * b.y;
+}
+
+// The output layer's six biases padded with zeros to its sixteen computed
+// channels, so every engine's epilogue adds them like a hidden layer's.
+__global__ void k_pad_bias(const float *__restrict__ b, int n, float *__restrict__ bp, int np) {
+    const int i = threadIdx.x;
+    if (i < np) bp[i] = i < n ? b[i] : 0.f;
 }
 
 // Master FP32 parameters in the oracle's layout ([Cout][Cin][27] weights)
@@ -920,6 +940,7 @@ struct dns_net_ctx {
     // activations for one sample
     __nv_bfloat16 *X0 = nullptr, *A1 = nullptr, *A2 = nullptr, *dY3 = nullptr, *dZ2 = nullptr, *dZ1 = nullptr;
     float *Z1 = nullptr, *Z2 = nullptr, *Y3 = nullptr, *wpart = nullptr;
+    float *b3p = nullptr;  // output biases padded to OUTP (zeros beyond the six)
     double *lpart = nullptr, *lsum = nullptr, *hostd = nullptr;
     int nchunk = 0;
     float in_scale = 1.f, out_scale = 1.f;  // closure use: input g * in_scale, tau = output * out_scale
@@ -935,7 +956,7 @@ static void net_release(dns_net_ctx *c) {
     if (!c) return;
     void *bufs[] = {c->p,   c->m,   c->v,    c->gw1,  c->gw2,  c->gw3, c->gb,  c->W1,  c->W2,    c->W3,
                     c->W2f, c->W3f, c->W1c,  c->W2c,  c->W3c,  c->W2fc, c->W3fc, c->err, c->X0,   c->A1,
-                    c->A2,  c->dY3, c->dZ2,  c->dZ1,  c->Z1,   c->Z2,  c->Y3,  c->wpart, c->lpart, c->lsum};
+                    c->A2,  c->dY3, c->dZ2,  c->dZ1,  c->Z1,   c->Z2,  c->Y3,  c->wpart, c->lpart, c->lsum, c->b3p};
     for (void *b : bufs)
         if (b) cudaFree(b);
     if (c->hostd) cudaFreeHost(c->hostd);
@@ -952,6 +973,7 @@ static cudaError_t net_pack(dns_net_ctx *c) {
     k_pack_canonical<32, OUTP><<<nblk(OUTP * 27 * 32), 256, 0, c->stream>>>(c->W3, c->W3c);
     k_pack_canonical<32, 32><<<nblk(32 * 27 * 32), 256, 0, c->stream>>>(c->W2f, c->W2fc);
     k_pack_canonical<OUTP, 32><<<nblk(32 * 27 * OUTP), 256, 0, c->stream>>>(c->W3f, c->W3fc);
+    k_pad_bias<<<1, 32, 0, c->stream>>>(c->p + OFF_B3, (int)NET_B3, c->b3p, OUTP);
     return cudaGetLastError();
 }
 
@@ -968,12 +990,19 @@ static cudaError_t conv_layer(dns_net_ctx *c, const __nv_bfloat16 *X, const __nv
     return conv<CIN, COUT, EPI>(c->n, X, W, bias, Z, A, Zp, st);
 }
 
-static cudaError_t net_forward_x0(dns_net_ctx *c, cudaStream_t st) {
-    cudaError_t e = conv_layer<16, 32, EPI_HIDDEN>(c, c->X0, c->W1, c->W1c, c->p + OFF_B1, c->Z1, c->A1, nullptr, st);
+// The three layers from X0; with ev (4 events) recorded before the first
+// layer and after each one, on st.
+static cudaError_t net_forward_x0(dns_net_ctx *c, cudaStream_t st, cudaEvent_t *ev = nullptr) {
+    cudaError_t e = ev ? cudaEventRecord(ev[0], st) : cudaSuccess;
+    if (e == cudaSuccess)
+        e = conv_layer<16, 32, EPI_HIDDEN>(c, c->X0, c->W1, c->W1c, c->p + OFF_B1, c->Z1, c->A1, nullptr, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[1], st);
     if (e == cudaSuccess)
         e = conv_layer<32, 32, EPI_HIDDEN>(c, c->A1, c->W2, c->W2c, c->p + OFF_B2, c->Z2, c->A2, nullptr, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess)
-        e = conv_layer<32, OUTP, EPI_OUT>(c, c->A2, c->W3, c->W3c, nullptr, c->Y3, nullptr, nullptr, st);
+        e = conv_layer<32, OUTP, EPI_OUT>(c, c->A2, c->W3, c->W3c, c->b3p, c->Y3, nullptr, nullptr, st);
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], st);
     return e;
 }
 
@@ -982,19 +1011,11 @@ __global__ void k_scale(float *g, int n, float s) {
     if (e < n) g[e] *= s;
 }
 
-// the last layer's bias (6 entries) on its padded output
-__global__ void k_add_bias_out(float *Y, long long V, const float *b) {
-    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (e < V * OUTP && (e % OUTP) < 6) Y[e] += b[e % OUTP];
-}
-
-static cudaError_t net_forward(dns_net_ctx *c, const float *g, cudaStream_t st) {
+static cudaError_t net_forward(dns_net_ctx *c, const float *g, cudaStream_t st, cudaEvent_t *ev = nullptr) {
     const long long V = (long long)c->n * c->n * c->n;
-    k_prep_input<<<nblk(V * 16), 256, 0, st>>>(g, V, c->X0);
-    cudaError_t e = net_forward_x0(c, st);
-    if (e != cudaSuccess) return e;
-    k_add_bias_out<<<nblk(V * OUTP), 256, 0, st>>>(c->Y3, V, c->p + OFF_B3);
-    return cudaGetLastError();
+    k_prep_input<<<nblk(V), 256, 0, st>>>(g, V, c->X0);
+    if (cudaError_t e = cudaGetLastError(); e != cudaSuccess) return e;
+    return net_forward_x0(c, st, ev);
 }
 
 // backward of the sample in flight (after net_forward), accumulating gradients
@@ -1085,6 +1106,7 @@ int dns_net_create(int n, unsigned long long seed, void *cuda_stream, dns_net *o
     al((void **)&c->Z1, 4 * V * 32);
     al((void **)&c->Z2, 4 * V * 32);
     al((void **)&c->Y3, 4 * V * OUTP);
+    al((void **)&c->b3p, sizeof(float) * OUTP);
     al((void **)&c->wpart, sizeof(float) * (size_t)c->nchunk * 27 * 32 * 32);
     al((void **)&c->lpart, sizeof(double) * 256);
     al((void **)&c->lsum, sizeof(double));
@@ -1183,10 +1205,53 @@ int dns_net_forward(dns_net net, const float *g, float *tau) {
     if (!net || !g || !tau) return DNS_ERR_ARG;
     const long long V = (long long)net->n * net->n * net->n;
     NK(net_forward(net, g, net->stream));
-    k_out_to_tau<<<nblk(6 * V), 256, 0, net->stream>>>(net->Y3, V, tau, 1.0f);
+    k_out_to_tau<<<nblk(V), 256, 0, net->stream>>>(net->Y3, V, tau, 1.0f);
     NK(cudaGetLastError());
     NK(cudaStreamSynchronize(net->stream));
     return net_status(net);
+}
+
+int dns_net_forward_profiled(dns_net net, const float *g, float *tau, int reps, double *layer_ms, double *total_ms) {
+    if (!net || !g || !tau || !layer_ms || !total_ms || reps < 1 || reps > 10000) return DNS_ERR_ARG;
+    const long long V = (long long)net->n * net->n * net->n;
+    // per forward: [0] before it, [1..4] before layer 1 and after each layer, [5] after it
+    std::vector<cudaEvent_t> ev(6 * (size_t)reps, nullptr);
+    int rc = DNS_OK;
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            rc = DNS_ERR_CUDA;
+            break;
+        }
+    for (int r = 0; r < reps && rc == DNS_OK; ++r) {
+        cudaEvent_t *er = ev.data() + 6 * (size_t)r;
+        if (cudaEventRecord(er[0], net->stream) != cudaSuccess || net_forward(net, g, net->stream, er + 1) != cudaSuccess)
+            rc = DNS_ERR_CUDA;
+        if (rc != DNS_OK) break;
+        k_out_to_tau<<<nblk(V), 256, 0, net->stream>>>(net->Y3, V, tau, 1.0f);
+        if (rc == DNS_OK && (cudaGetLastError() != cudaSuccess || cudaEventRecord(er[5], net->stream) != cudaSuccess))
+            rc = DNS_ERR_CUDA;
+    }
+    if (cudaStreamSynchronize(net->stream) != cudaSuccess) rc = DNS_ERR_CUDA;
+    if (rc == DNS_OK) {
+        double acc[3] = {0, 0, 0};
+        float ms = 0.f;
+        for (int r = 0; r < reps && rc == DNS_OK; ++r) {
+            const cudaEvent_t *er = ev.data() + 6 * (size_t)r;
+            for (int l = 0; l < 3 && rc == DNS_OK; ++l) {
+                if (cudaEventElapsedTime(&ms, er[1 + l], er[2 + l]) != cudaSuccess) rc = DNS_ERR_CUDA;
+                acc[l] += ms;
+            }
+        }
+        if (rc == DNS_OK && cudaEventElapsedTime(&ms, ev[0], ev[6 * (size_t)reps - 1]) != cudaSuccess) rc = DNS_ERR_CUDA;
+        if (rc == DNS_OK) {
+            for (int l = 0; l < 3; ++l) layer_ms[l] = acc[l] / reps;
+            *total_ms = (double)ms / reps;
+        }
+    }
+    for (auto &e : ev)
+        if (e) cudaEventDestroy(e);
+    return rc == DNS_OK ? net_status(net) : rc;
 }
 
 int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count) {
@@ -1314,7 +1379,7 @@ cudaError_t les_closure_forcing(LesClosure *c, const Geo &g, const void *U, void
     if (c->net) {
         k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, c->net->in_scale);
         if ((e = net_forward(c->net, c->gr, st)) != cudaSuccess) return e;
-        k_out_to_tau<<<nblk(6 * V), 256, 0, st>>>(c->net->Y3, V, c->tau, c->net->out_scale);
+        k_out_to_tau<<<nblk(V), 256, 0, st>>>(c->net->Y3, V, c->tau, c->net->out_scale);
     } else {
         k_real_part<<<nblk(9 * V), 256, 0, st>>>(c->gc, 9 * V, c->gr, 1.0f);
         k_smagorinsky<<<nblk(V), 256, 0, st>>>(c->gr, V, c->smag_c2, c->tau);

@@ -71,6 +71,7 @@ SIGNATURES = {
     "dns_net_get_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "dns_net_set_params": (_i, [_vp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "dns_net_forward": (_i, [_vp, _vp, _vp]),
+    "dns_net_forward_profiled": (_i, [_vp, _vp, _vp, _i, _dp, _dp]),
     "dns_net_gradients": (_i, [_vp, _vp, _vp, _dp, ctypes.POINTER(ctypes.c_float), ctypes.c_long]),
     "dns_net_train_step": (_i, [_vp, _i, _vp, _vp, _d, _dp]),
     "dns_les_builder_create": (_i, [_i, _i, ctypes.POINTER(_vp)]),
@@ -599,6 +600,15 @@ def dns_net_set_params(net: int, params) -> None:
 
 def dns_net_forward(net: int, g, tau) -> None:
     _check(load().dns_net_forward(net, _dev(g), _dev(tau)), "dns_net_forward")
+
+
+def dns_net_forward_profiled(net: int, g, tau, reps: int):
+    """(per-layer mean device ms [3], mean device ms per whole forward)."""
+    arr = (ctypes.c_double * 3)()
+    tot = ctypes.c_double()
+    _check(load().dns_net_forward_profiled(net, _dev(g), _dev(tau), int(reps), arr, ctypes.byref(tot)),
+           "dns_net_forward_profiled")
+    return list(arr), tot.value
 
 
 def dns_net_gradients(net: int, g, tau, want_grad: bool = True):

@@ -274,8 +274,11 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
     """Cost of the learned closure on the GPU: the network forward on one n^3
     sample (flops = 2 n^3 27 (9*32 + 32*32 + 32*6), the contraction the
     tensor cores run; the input channels are padded to 16 and the output to
-    16 on the device, which is not counted) on both convolution engines (the
-    rest uses the default one), one Adam training step per
+    16 on the device, which is not counted) on every convolution engine (the
+    rest uses the default one) -- per call of dns_net_forward, which
+    synchronises and reads the status word, and as device time of the three
+    convolution layers and of whole forwards queued back to back
+    (dns_net_forward_profiled) --, one Adam training step per
     sample, and one LES step at n^3 without a model, with Smagorinsky and
     with the learned closure, next to one DNS step at dns_N^3.  Times by CUDA
     events on the default stream (forward) and wall clock around
@@ -304,24 +307,39 @@ def les_bench(n: int = 64, reps: int = 20, batch: int = 8, dns_N: int = 256) -> 
             b.synchronize()
             return a.elapsed_time(b) / reps
 
+        def time_device(tag):
+            # device time of the convolution layers and of whole forwards
+            # queued back to back (no host synchronisation between them)
+            layer_ms, total_ms = dns.dns_net_forward_profiled(net, g, tau, reps)
+            conv_ms = sum(layer_ms)
+            out[f"conv_layer_ms_{tag}"] = layer_ms
+            out[f"conv_ms_{tag}"] = conv_ms
+            out[f"conv_tflops_{tag}"] = flops / (conv_ms / 1e3) / 1e12
+            out[f"forward_device_ms_{tag}"] = total_ms
+
         dns.dns_net_set_engine(net, dns.DNS_CONV_TCGEN05)
         fwd_tc = time_forward()
         out["forward_ms_tcgen05"] = fwd_tc
         out["forward_tflops_tcgen05"] = flops / (fwd_tc / 1e3) / 1e12
+        time_device("tcgen05")
         dns.dns_net_set_engine(net, dns.DNS_CONV_TCGEN05_SLAB)
         fwd_slab = time_forward()
         out["forward_ms_tcgen05_slab"] = fwd_slab
         out["forward_tflops_tcgen05_slab"] = flops / (fwd_slab / 1e3) / 1e12
+        time_device("tcgen05_slab")
         dns.dns_net_set_engine(net, dns.DNS_CONV_MMA_SYNC)
         fwd = time_forward()
         out["forward_ms_mma_sync"] = fwd
         out["forward_tflops_mma_sync"] = flops / (fwd / 1e3) / 1e12
+        time_device("mma_sync")
         # the rest runs on the engine the network is created with
         dns.dns_net_set_engine(net, default_engine)
         out["engine"] = {0: "mma_sync", 1: "tcgen05", 2: "tcgen05_slab"}[default_engine]
         fwd = {0: fwd, 1: fwd_tc, 2: fwd_slab}[default_engine]
         out["forward_ms"] = fwd
         out["forward_tflops"] = flops / (fwd / 1e3) / 1e12
+        out["conv_ms"] = out["conv_ms_" + out["engine"]]
+        out["conv_tflops"] = out["conv_tflops_" + out["engine"]]
         dns.dns_net_train_step(net, batch, G, T, 1e-4)
         torch.cuda.synchronize()
         t0 = time.perf_counter()

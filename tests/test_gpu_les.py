@@ -365,3 +365,27 @@ def test_trained_closure_gains_over_no_model(dns):
     assert min(rep["a_priori_correlation"].values()) > 0.6
     assert post["learned"]["log_spectrum_err"] < 0.5 * post["no_model"]["log_spectrum_err"]
     assert abs(post["learned"]["E"] - post["filtered_dns"]["E"]) < abs(post["no_model"]["E"] - post["filtered_dns"]["E"])
+
+
+@pytest.mark.parametrize("engine", ENGINES)
+def test_profiled_forward_gives_the_forward_and_its_layer_times(dns, engine):
+    # the profiled entry point queues the same forward (same kernels, same
+    # buffers), so its output is bit-identical to dns_net_forward's; its
+    # layer times are positive and add up to less than the whole forward
+    n = 32
+    gen = torch.Generator(device="cuda").manual_seed(13)
+    g = torch.randn((9, n, n, n), device="cuda", generator=gen)
+    net = dns.dns_net_create(n, seed=14)
+    try:
+        dns.dns_net_set_engine(net, engine)
+        t1 = torch.empty((6, n, n, n), device="cuda")
+        t2 = torch.full((6, n, n, n), float("nan"), device="cuda")
+        dns.dns_net_forward(net, g, t1)
+        layer_ms, total_ms = dns.dns_net_forward_profiled(net, g, t2, 5)
+        assert torch.equal(t1, t2)
+        assert all(t > 0 for t in layer_ms) and total_ms > 0
+        assert sum(layer_ms) <= total_ms * 1.01
+        with pytest.raises(dns.DnsError):
+            dns.dns_net_forward_profiled(net, g, t2, 0)
+    finally:
+        dns.dns_net_free(net)
