@@ -62,7 +62,8 @@ enum dns_status {
     DNS_ERR_TIMEOUT = 4,     /* a bounded device wait gave up */
     DNS_ERR_NONFINITE = 5,   /* NaN or Inf found in the state */
     DNS_ERR_UNSUPPORTED = 6, /* N, dtype or option not supported */
-    DNS_ERR_GUARD = 7        /* a guard region around a device buffer was overwritten */
+    DNS_ERR_GUARD = 7,       /* a guard region around a device buffer was overwritten */
+    DNS_ERR_INDEX = 8        /* index-checked build: a kernel met an address outside every buffer */
 };
 
 /* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 8, 12,
@@ -168,6 +169,31 @@ int dns_check_guards(dns_handle h);
  * set, as a real timeout does; the CUDA context stays usable.  For tests of
  * the error path; faults nothing. */
 int dns_check_wait_timeout(dns_handle h, double seconds);
+
+/* Index-checked build (no counterpart in the paper; a bounds checker for
+ * systems without a memory checker).  The library can also be compiled as
+ * libdns_checked.so (-DDNS_CHECKED; the mesh sizes 16, 24, 36, 64, 96, 128,
+ * 256 and 512 only, others return DNS_ERR_UNSUPPORTED), whose solver
+ * kernels -- every pass of the right-hand side and of the RK4 update, the
+ * layout conversions, curl and diagnostics, and the source of every bulk
+ * copy -- compare each global address they are about to use with the
+ * handle's buffers (guard regions excluded) and, for the duration of a call
+ * given device buffers, the caller's.  An address outside all of them is
+ * not accessed (a load reads zero, a store or copy is skipped); the first
+ * one is recorded, and dns_synchronize / dns_ensemble_synchronize return
+ * DNS_ERR_INDEX from then on.  The learned-closure kernels are not checked.
+ *
+ * dns_checked_build: 1 in the checked library, 0 otherwise.
+ * dns_first_bad_access: after draining the handle's stream, the source
+ * line of the check that rejected the first address and that address
+ * (0, 0 if none was rejected).
+ * dns_check_index_selftest: queues a one-thread kernel that hands the
+ * check the address one byte past the end of the handle's largest buffer
+ * (compared, never accessed), so that the next dns_synchronize returns
+ * DNS_ERR_INDEX; DNS_ERR_UNSUPPORTED in the unchecked library. */
+int dns_checked_build(void);
+int dns_first_bad_access(dns_handle h, int *line, unsigned long long *address);
+int dns_check_index_selftest(dns_handle h);
 
 /* Diagnostics of the current state, accumulated in double (synchronising):
  * E = <|u|^2>/2, eps = nu <|grad u|^2>, and the shell spectrum

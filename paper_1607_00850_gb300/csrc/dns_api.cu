@@ -59,7 +59,8 @@ struct dns_ctx {
     void *Om = nullptr, *rom = nullptr;  // curl of the stage input (state boxes / rhs input)
     double *partials = nullptr, *sums = nullptr, *Ek = nullptr;
     double *nu_box = nullptr;  // per-box viscosity when several boxes share the context
-    int *err = nullptr;        // device status word of bounded waits (Geo::err)
+    int *err = nullptr;        // device status word: [0] code, [1] source line, [2..3] address (Geo::err)
+    unsigned long long *rng = nullptr;  // device table of the address ranges kernels may touch (checked builds)
     int nblk = 0, smax = 0;
     double *host = nullptr;  // pinned read-back area
     cudaGraph_t graph = nullptr;
@@ -98,6 +99,35 @@ static const double RK_B[3] = {0.5, 0.5, 1.0};
 
 static void drop_async_io(dns_ctx *h);
 
+// Index-checked builds: the device table of address ranges (its layout in
+// dns_check.cuh) lists every device buffer of the handle without its guard
+// regions, plus up to two caller buffers of the call in progress.  Rewritten
+// (synchronously) whenever a buffer is allocated or freed and around calls
+// that hand the kernels a caller's device buffer.  A no-op otherwise.
+static void refresh_ranges(dns_ctx *h, const void *p1 = nullptr, size_t b1 = 0, const void *p2 = nullptr,
+                           size_t b2 = 0) {
+#ifdef DNS_CHECKED
+    if (!h->rng) return;
+    std::vector<unsigned long long> t(1, 0ull);
+    auto add = [&](const void *p, size_t b) {
+        if (!p || !b || t[0] >= (unsigned long long)dns::kMaxCheckRanges) return;
+        t.push_back((unsigned long long)p);
+        t.push_back((unsigned long long)p + b);
+        ++t[0];
+    };
+    for (const GuardedAlloc &a : h->allocs) add(a.user, a.bytes);
+    add(p1, b1);
+    add(p2, b2);
+    cudaMemcpy(h->rng, t.data(), t.size() * sizeof(unsigned long long), cudaMemcpyHostToDevice);
+#else
+    (void)h;
+    (void)p1;
+    (void)b1;
+    (void)p2;
+    (void)b2;
+#endif
+}
+
 static void release(dns_ctx *h) {
     if (!h) return;
     if (h->exec) cudaGraphExecDestroy(h->exec);
@@ -107,6 +137,7 @@ static void release(dns_ctx *h) {
     drop_async_io(h);
     for (const GuardedAlloc &a : h->allocs) cudaFree(a.base);
     h->allocs.clear();
+    if (h->rng) cudaFree(h->rng);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
     delete h;
 }
@@ -129,6 +160,7 @@ static int dev_alloc(dns_ctx *h, void **p, size_t bytes) {
     h->allocs.push_back({base, user, bytes});
     h->bytes += (long long)bytes;
     *p = user;
+    refresh_ranges(h);
     return DNS_OK;
 }
 
@@ -138,6 +170,7 @@ static void dev_free(dns_ctx *h, void *p) {
             cudaFree(h->allocs[i].base);
             h->bytes -= (long long)h->allocs[i].bytes;
             h->allocs.erase(h->allocs.begin() + (long)i);
+            refresh_ranges(h);
             return;
         }
 }
@@ -188,12 +221,13 @@ static cudaError_t to_full(const dns_ctx *h, const void *cmp, void *full) {
 
 // elementwise copy between compact buffers of different complex types
 template <typename Tin, typename Tout>
-__global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ b, long long n) {
+__global__ void k_convert(const Tin *__restrict__ a, Tout *__restrict__ b, long long n, dns::Chk ck) {
     for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        const Tin v = DNS_LD(ck, a + e);
         Tout o;
-        o.x = a[e].x;
-        o.y = a[e].y;
-        b[e] = o;
+        o.x = v.x;
+        o.y = v.y;
+        DNS_ST(ck, b + e, o);
     }
 }
 
@@ -307,10 +341,13 @@ static int set_state(dns_ctx *h, int b, const void *uhat, int on_device) {
     if (!on_device) {
         CK(cudaMemcpyAsync(h->io, uhat, bytes, cudaMemcpyHostToDevice, h->stream));
         src = h->io;
+    } else {
+        refresh_ranges(h, uhat, bytes);
     }
     CK(full_to_state(h, src, box_ptr(h->U, h->g.bS, h->creal, b), box_ptr(h->U0, h->g.bS, h->cacc, b)));
     CK(curl_box(h, b));
     CK(cudaStreamSynchronize(h->stream));
+    if (on_device) refresh_ranges(h);
     return DNS_OK;
 }
 
@@ -318,12 +355,14 @@ static int get_state(dns_ctx *h, int b, void *uhat, int on_device) {
     const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
     const void *u0 = box_ptr(h->U0, h->g.bS, h->cacc, b);
     if (on_device) {
+        refresh_ranges(h, uhat, bytes);
         CK(acc_to_full(h, u0, uhat));
     } else {
         CK(acc_to_full(h, u0, h->io));
         CK(cudaMemcpyAsync(uhat, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    if (on_device) refresh_ranges(h);
     return DNS_OK;
 }
 
@@ -364,6 +403,16 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
         delete h;
         return DNS_ERR_UNSUPPORTED;
     }
+#ifdef DNS_CHECKED
+    // the address-range table, filled by every dev_alloc below
+    if (cudaMalloc((void **)&h->rng, sizeof(unsigned long long) * (1 + 2 * dns::kMaxCheckRanges)) != cudaSuccess ||
+        cudaMemset(h->rng, 0, sizeof(unsigned long long)) != cudaSuccess) {
+        cudaGetLastError();
+        if (h->rng) cudaFree(h->rng);
+        delete h;
+        return DNS_ERR_OOM;
+    }
+#endif
     const int K = (N - 1) / 3;
     Geo &g = h->g;
     g.N = N;
@@ -401,8 +450,9 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
     if (!rc) rc = dev_alloc(h, (void **)&h->sums, sizeof(double) * 2);
     if (!rc) rc = dev_alloc(h, (void **)&h->Ek, sizeof(double) * h->smax);
     if (!rc && nb > 1) rc = dev_alloc(h, (void **)&h->nu_box, sizeof(double) * nb);
-    if (!rc) rc = dev_alloc(h, (void **)&h->err, sizeof(int));
+    if (!rc) rc = dev_alloc(h, (void **)&h->err, 4 * sizeof(int));
     g.err = h->err;
+    g.rng = h->rng;
     if (!rc && cudaMallocHost((void **)&h->host, sizeof(double) * (4 + h->smax)) != cudaSuccess) {
         h->host = nullptr;
         rc = DNS_ERR_OOM;
@@ -438,7 +488,7 @@ static int ctx_create(int N, int nb, const double *nu_host, double dt, int dtype
     }
     if (e == cudaSuccess && nb > 1)
         e = cudaMemcpy(h->nu_box, nu_host, sizeof(double) * nb, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, sizeof(int), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->err, 0, 4 * sizeof(int), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U, 0, nb * 3 * g.sS * h->creal, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U0, 0, nb * 3 * g.sS * h->cacc, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->U1, 0, nb * 3 * g.sS * h->cacc, h->stream);
@@ -473,6 +523,7 @@ const char *dns_strerror(int status) {
         case DNS_ERR_NONFINITE: return "non-finite value in the state";
         case DNS_ERR_UNSUPPORTED: return "unsupported size, dtype or option";
         case DNS_ERR_GUARD: return "a guard region around a device buffer was overwritten";
+        case DNS_ERR_INDEX: return "a kernel of the index-checked build met an address outside every buffer";
         default: return "unknown status";
     }
 }
@@ -504,7 +555,7 @@ int dns_check_guards(dns_handle h) {
 static int poll_device_status(dns_ctx *h) {
     int v = 0;
     CK(cudaMemcpy(&v, h->err, sizeof(int), cudaMemcpyDeviceToHost));
-    return v ? DNS_ERR_TIMEOUT : DNS_OK;
+    return v == 0 ? DNS_OK : (v == dns::kErrIndex ? DNS_ERR_INDEX : DNS_ERR_TIMEOUT);
 }
 
 int dns_synchronize(dns_handle h) {
@@ -534,6 +585,49 @@ extern "C" int dns_check_wait_timeout(dns_handle h, double seconds) {
     if (!h || !(seconds > 0.0) || !(seconds <= 2.0)) return DNS_ERR_ARG;
     k_wait_timeout_check<<<1, 32, 0, h->stream>>>(h->err, (unsigned long long)(seconds * 1e9));
     CK(cudaGetLastError());
+    return DNS_OK;
+}
+
+// The index check exercised on purpose: one thread hands the check the
+// address one byte past the end of buffer B.  The check compares addresses
+// only; nothing is read or written there, and the check records the
+// rejected address and this source line in the status word.
+__global__ void k_index_check_selftest(dns::Chk ck, const unsigned char *probe) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const bool ok = DNS_RANGE_OK(ck, probe, 1);
+        (void)ok;
+    }
+}
+
+extern "C" int dns_checked_build(void) {
+#ifdef DNS_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+extern "C" int dns_check_index_selftest(dns_handle h) {
+    if (!h) return DNS_ERR_ARG;
+#ifdef DNS_CHECKED
+    const unsigned char *end = static_cast<const unsigned char *>(h->B) + (size_t)h->g.nb * 6 * h->g.sB * h->creal;
+    k_index_check_selftest<<<1, 32, 0, h->stream>>>(h->g.chk(), end);
+    CK(cudaGetLastError());
+    return DNS_OK;
+#else
+    return DNS_ERR_UNSUPPORTED;
+#endif
+}
+
+extern "C" int dns_first_bad_access(dns_handle h, int *line, unsigned long long *address) {
+    if (!h || !line || !address) return DNS_ERR_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    int w[4] = {0, 0, 0, 0};
+    CK(cudaMemcpy(w, h->err, sizeof(w), cudaMemcpyDeviceToHost));
+    unsigned long long a = 0;
+    std::memcpy(&a, w + 2, sizeof(a));
+    *line = w[0] == dns::kErrIndex ? w[1] : 0;
+    *address = w[0] == dns::kErrIndex ? a : 0ull;
     return DNS_OK;
 }
 
@@ -631,6 +725,8 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
     if (!on_device) {
         CK(cudaMemcpyAsync(h->io, u, bytes, cudaMemcpyHostToDevice, h->stream));
         src = h->io;
+    } else {
+        refresh_ranges(h, u, bytes);
     }
     CK(h->ps.zfwd(h->g, h->tw, src, h->B, h->stream));
     CK(h->ps.p4[h->plan[3]](h->g, h->tw, h->B, h->A, h->stream));
@@ -643,11 +739,13 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
     if (h->same_type) {
         CK(cudaMemcpyAsync(h->U, h->rout, (size_t)n * h->cacc, cudaMemcpyDeviceToDevice, h->stream));
     } else {
-        k_convert<double2, float2><<<grid_for(n), 256, 0, h->stream>>>((const double2 *)h->rout, (float2 *)h->U, n);
+        k_convert<double2, float2><<<grid_for(n), 256, 0, h->stream>>>((const double2 *)h->rout, (float2 *)h->U, n,
+                                                                        h->g.chk());
         CK(cudaGetLastError());
     }
     CK(curl_box(h, 0));
     CK(cudaStreamSynchronize(h->stream));
+    if (on_device) refresh_ranges(h);
     return DNS_OK;
 }
 
@@ -663,6 +761,8 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
     if (!on_device) {
         CK(cudaMemcpyAsync(h->io, uhat_in, bytes, cudaMemcpyHostToDevice, h->stream));
         src = h->io;
+    } else {
+        refresh_ranges(h, uhat_in, bytes, duhat_out, bytes);
     }
     CK(full_to_state(h, src, h->rin, nullptr));
     Geo g1 = h->g;
@@ -686,6 +786,7 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
         CK(cudaMemcpyAsync(duhat_out, h->io, bytes, cudaMemcpyDeviceToHost, h->stream));
     }
     CK(cudaStreamSynchronize(h->stream));
+    if (on_device) refresh_ranges(h);
     return DNS_OK;
 }
 

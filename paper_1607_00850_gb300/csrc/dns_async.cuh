@@ -75,8 +75,9 @@ __device__ __forceinline__ void bulk_copy_g2s(void *dst_smem, const void *src, u
         : "memory");
 }
 
+// The first code recorded stays (a later failure does not overwrite it).
 __device__ __forceinline__ void record_error(int *err, int code) {
-    if (err) atomicExch(err, code);
+    if (err) atomicCAS(err, 0, code);
 }
 
 }  // namespace dns

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "dns_check.cuh"
+
 namespace dns {
 
 template <typename R> struct CT;
@@ -335,7 +337,7 @@ __host__ __device__ constexpr int twt_size(int N, int MAXR, bool rev = false) {
 // Kernels that also run the reversed plan keep its tables right after the
 // forward plan's: tw [N] | forward tables | reversed tables.
 template <typename cplx, int N, int MAXR, bool REV = false, int S = 1>
-__device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg) {
+__device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg, const Chk &ck = Chk{}) {
     constexpr FftPlan P = plan_of(N, MAXR, REV);
     if constexpr (S < P.nst) {
         constexpr int R = P.r[S], Ns = P.ns[S], TWS = N / (Ns * R), off = twt_offset(N, MAXR, S, REV);
@@ -345,9 +347,9 @@ __device__ __forceinline__ void build_twt(cplx *twt, const cplx *twg) {
             int r = 0;  // padding entries repeat w^0
             if (i < R1 - 1) r = i + 1;
             else if (i < R1 - 1 + R / R1 - 1) r = R1 * (i - (R1 - 1) + 1);
-            twt[off + e] = twg[r * k * TWS];
+            twt[off + e] = DNS_LD(ck, twg + r * k * TWS);
         }
-        build_twt<cplx, N, MAXR, REV, S + 1>(twt, twg);
+        build_twt<cplx, N, MAXR, REV, S + 1>(twt, twg, ck);
     }
 }
 // The R - 1 twiddles w^(r k TWS), r = 1..R-1, of one work item from its row

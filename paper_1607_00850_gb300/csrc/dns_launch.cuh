@@ -249,6 +249,15 @@ template <typename real, typename acc> struct UpdLaunch {
         a.stage = e.stage;
         a.dt = e.dt;
         a.ifrk = e.ifrk;
+        a.rng = nullptr;
+        a.err = nullptr;
+        return a;
+    }
+    // the same with the context's range table and status word (checked accesses)
+    static UpdateArgs<real, acc> args(const UpdateArgsErased &e, const Geo &g) {
+        UpdateArgs<real, acc> a = args(e);
+        a.rng = g.rng;
+        a.err = g.err;
         return a;
     }
 };
@@ -260,7 +269,7 @@ template <typename real, typename acc, int N> struct UpdLaunchN {
         static_assert(GeoN<N>::sS < (1ll << 31), "one field's stored modes index with int");
         if (g.nb < 1 || g.nb > 65535) return cudaErrorInvalidValue;
         const dim3 grid((unsigned)((GeoN<N>::sS + 255) / 256), (unsigned)g.nb);
-        k_p5b_update<real, acc, N><<<grid, 256, 0, st>>>((const cplx *)Nh, UpdLaunch<real, acc>::args(e));
+        k_p5b_update<real, acc, N><<<grid, 256, 0, st>>>((const cplx *)Nh, UpdLaunch<real, acc>::args(e, g));
         return cudaGetLastError();
     }
 };
@@ -295,7 +304,7 @@ template <typename real, typename acc, int N, int V> struct FusedLaunch {
     static cudaError_t p5f(const Geo &g, const void *tw, const void *A, const UpdateArgsErased &e, cudaStream_t st) {
         dim3 grid(g.nb, cdiv(g.Kz, S::W), g.Kx);
         k_p5_fused<real, acc, N, S::W, S::T, S::RC><<<grid, S::T, S::smem, st>>>(
-            g, (const cplx *)tw, (const cplx *)A, UpdLaunch<real, acc>::args(e));
+            g, (const cplx *)tw, (const cplx *)A, UpdLaunch<real, acc>::args(e, g));
         return cudaGetLastError();
     }
     static cudaError_t prepare() { return set_smem(k_p5_fused<real, acc, N, S::W, S::T, S::RC>, S::smem); }

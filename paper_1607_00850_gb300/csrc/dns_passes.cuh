@@ -40,6 +40,8 @@ struct Geo {
     int nb;        // boxes of this size advanced together (batch), >= 1
     long long bS, bA, bB;  // elements between consecutive boxes in the state, A and B
     int *err;      // device status word: a bounded wait that gave up writes its code here
+    const unsigned long long *rng;  // address ranges of the handle (index-checked builds), or nullptr
+    __host__ __device__ Chk chk() const { return Chk{rng, err}; }
 };
 
 // The dealiased geometry is a function of N alone (K = floor((N - 1) / 3), the
@@ -75,6 +77,8 @@ struct UpdateArgs {
     double dt;       // time step (integrating-factor scheme)
     int stage;
     int ifrk;        // 1: integrating-factor RK4 (exact viscous factor), 0: classical RK4
+    const unsigned long long *rng;  // address ranges of the handle (index-checked builds), or nullptr
+    int *err;        // the handle's device status word
 };
 
 __device__ __forceinline__ int compact_to_k(int i, int K) { return i <= K ? i : i - (2 * K + 1); }
@@ -88,8 +92,8 @@ template <int N> __device__ __forceinline__ int row_to_compact(int n, int K) {
 
 template <typename real> __device__ __forceinline__ void load_twiddles(typename CT<real>::t *tw,
                                                                        const typename CT<real>::t *twg,
-                                                                       int N) {
-    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = twg[i];
+                                                                       int N, const Chk &ck = Chk{}) {
+    for (int i = threadIdx.x; i < N; i += blockDim.x) tw[i] = DNS_LD(ck, twg + i);
 }
 
 // ------------------------------------------------------------------- bulk-fed column tiles
@@ -100,15 +104,18 @@ template <typename real> __device__ __forceinline__ void load_twiddles(typename 
 // tid, tid + T, ...); rows_wait waits (bounded, one thread) and returns false
 // after recording the timeout, in which case the block must return.
 template <typename cplx, int W>
-__device__ __forceinline__ void rows_issue(cplx *stage, const cplx *src, long long stride, int nrows, int ncols,
-                                           uint64_t *bar) {
+__device__ __forceinline__ void rows_issue(const Geo &g, cplx *stage, const cplx *src, long long stride, int nrows,
+                                           int ncols, uint64_t *bar) {
     const uint32_t rb = (uint32_t)(ncols * sizeof(cplx));
     if (threadIdx.x == 0) {
         mbar_init(bar, 1);
         mbar_arrive_expect_tx(bar, rb * (uint32_t)nrows);
     }
     __syncthreads();
-    for (int r = threadIdx.x; r < nrows; r += blockDim.x) bulk_copy_g2s(stage + r * W, src + r * stride, rb, bar);
+    // a row outside the handle's buffers (checked builds) is not copied; the
+    // block's bounded wait then gives up
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x)
+        if (DNS_RANGE_OK(g, src + r * stride, rb)) bulk_copy_g2s(stage + r * W, src + r * stride, rb, bar);
 }
 
 __device__ __forceinline__ bool rows_wait(uint64_t *bar, int *s_ok, int *err) {
@@ -145,8 +152,8 @@ __global__ void __launch_bounds__(T) k_p1_xinv(Geo g, const typename CT<real>::t
     constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const cplx *src = (f < 3 ? U + f * GeoN<N>::sS : Om + (f - 3) * GeoN<N>::sS) + box * GeoN<N>::bS + (long long)jy * Kzp;
     cplx *dst = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)jy * Kzp;
-    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, Kx, min(W, Kzp - kz0), &bar);
-    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) rows_issue<cplx, W>(g, tile, src + kz0, (long long)Kx * Kzp, Kx, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N, g.chk());
     if constexpr (BULK) {
         if (!rows_wait(&bar, &s_ok, g.err)) return;
     } else {
@@ -156,12 +163,12 @@ __global__ void __launch_bounds__(T) k_p1_xinv(Geo g, const typename CT<real>::t
         const int kz = kz0 + c;
         const int ix = row_to_compact<N>(n, K);
         if (kz >= Kz || ix < 0) return cmk<cplx>(0.0, 0.0);
-        const cplx v = BULK ? tile[ix * W + c] : src[(long long)ix * Kx * Kzp + kz];
+        const cplx v = BULK ? tile[ix * W + c] : DNS_LD(g, src + (long long)ix * Kx * Kzp + kz);
         return cmk<cplx>(v.x * scale, v.y * scale);
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
-        if (kz < Kz) dst[(long long)n * Kx * Kzp + kz] = v;
+        if (kz < Kz) DNS_ST(g, dst + (long long)n * Kx * Kzp + kz, v);
     };
     TileFFT<real, N, W, T, +1, MAXR>::run(tile, W, tw, load, store);
 }
@@ -188,15 +195,18 @@ __global__ void k_curl(Geo g, const typename CT<real>::t *__restrict__ U, typena
     const int iy = (int)(r % g.Kx), ix = (int)(r / g.Kx);
     const long long m = box * g.bS + mm;
     if (kz >= g.Kz) {
-        Om[m] = Om[sS + m] = Om[2 * sS + m] = cmk<cplx>(0.0, 0.0);
+        const cplx z = cmk<cplx>(0.0, 0.0);
+        DNS_ST(g, Om + m, z);
+        DNS_ST(g, Om + sS + m, z);
+        DNS_ST(g, Om + 2 * sS + m, z);
         return;
     }
     cplx ox, oy, oz;
-    curl_mode<cplx, real>((real)compact_to_k(ix, g.K), (real)compact_to_k(iy, g.K), (real)kz, U[m], U[sS + m],
-                          U[2 * sS + m], ox, oy, oz);
-    Om[m] = ox;
-    Om[sS + m] = oy;
-    Om[2 * sS + m] = oz;
+    curl_mode<cplx, real>((real)compact_to_k(ix, g.K), (real)compact_to_k(iy, g.K), (real)kz, DNS_LD(g, U + m),
+                          DNS_LD(g, U + sS + m), DNS_LD(g, U + 2 * sS + m), ox, oy, oz);
+    DNS_ST(g, Om + m, ox);
+    DNS_ST(g, Om + sS + m, oy);
+    DNS_ST(g, Om + 2 * sS + m, oz);
 }
 
 // ------------------------------------------------------------------- P2
@@ -214,8 +224,8 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
     constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const cplx *src = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)x * Kx * Kzp;
     cplx *dst = B + box * GeoN<N>::bB + f * GeoN<N>::sB + (long long)x * N * Kzp;
-    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, Kx, min(W, Kzp - kz0), &bar);
-    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) rows_issue<cplx, W>(g, tile, src + kz0, Kzp, Kx, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N, g.chk());
     if constexpr (BULK) {
         if (!rows_wait(&bar, &s_ok, g.err)) return;
     } else {
@@ -228,11 +238,11 @@ __global__ void __launch_bounds__(T) k_p2_yinv(Geo g, const typename CT<real>::t
         z.x = 0;
         z.y = 0;
         if (kz >= Kz || iy < 0) return z;
-        return BULK ? tile[iy * W + c] : src[(long long)iy * Kzp + kz];
+        return BULK ? tile[iy * W + c] : DNS_LD(g, src + (long long)iy * Kzp + kz);
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
-        if (kz < Kz) dst[(long long)n * Kzp + kz] = v;
+        if (kz < Kz) DNS_ST(g, dst + (long long)n * Kzp + kz, v);
     };
     TileFFT<real, N, W, T, +1, MAXR>::run(tile, W, tw, load, store);
 }
@@ -296,9 +306,9 @@ __device__ __forceinline__ void p3_fwd_rest_store(const Geo &g, typename CT<real
         const cplx zb = tile[(L + l) * LDR + radd(kz)];
         const long long off = (line0 + l) * Kzp + kz;
         // X = (Z[k] + conj Z[N-k]) / 2,  Y = (Z[k] - conj Z[N-k]) / (2i)
-        B[off] = cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y));
-        B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
-        B[2 * sB + off] = zb;
+        DNS_ST(g, B + off, cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y)));
+        DNS_ST(g, B + sB + off, cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x)));
+        DNS_ST(g, B + 2 * sB + off, zb);
     }
 }
 
@@ -440,8 +450,8 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);  // N twiddles, then the per-stage tables
     cplx *tile = tw + N + twt_size(N, MAXR);         // [3L][LDR]: pair p of line l at row p*L + l
-    load_twiddles<real>(tw, twg, N);
-    build_twt<cplx, N, MAXR>(tw + N, twg);
+    load_twiddles<real>(tw, twg, N, g.chk());
+    build_twt<cplx, N, MAXR>(tw + N, twg, g.chk());
     __syncthreads();
     constexpr int K = GeoN<N>::K, Kzp = GeoN<N>::Kzp;
     const long long lineg = (long long)blockIdx.x * L;  // = box*N*N + x*N + y0
@@ -454,7 +464,8 @@ __device__ __forceinline__ void p3_body(Geo g, const typename CT<real>::t *__res
         const int kz = n <= N / 2 ? n : N - n;
         if (kz > K) return cmk<cplx>(0.0, 0.0);
         const long long off = (line0 + l) * Kzp + kz;
-        return p3_pack<N>(B[P3Pairs<N>::fa(p) * sB + off], B[P3Pairs<N>::fb(p) * sB + off], p, n, kz);
+        return p3_pack<N>(DNS_LD(g, B + P3Pairs<N>::fa(p) * sB + off), DNS_LD(g, B + P3Pairs<N>::fb(p) * sB + off), p,
+                          n, kz);
     };
     auto tstore = [&](int vl, int n, cplx v) { tile[vl * LDR + radd(n)] = v; };
     RowFFT<real, N, 3 * L, T, +1, MAXR, 0, false, true>::run(tile, tw, iload, tstore);
@@ -503,7 +514,8 @@ __device__ __forceinline__ void p3_issue(const Geo &g, const typename CT<real>::
     mbar_arrive_expect_tx(bar, (uint32_t)(6 * PS::field_bytes));
 #pragma unroll
     for (int f = 0; f < 6; ++f)
-        bulk_copy_g2s(stage + f * (L * PS::KZP), src + f * GeoN<N>::sB, (uint32_t)PS::field_bytes, bar);
+        if (DNS_RANGE_OK(g, src + f * GeoN<N>::sB, PS::field_bytes))
+            bulk_copy_g2s(stage + f * (L * PS::KZP), src + f * GeoN<N>::sB, (uint32_t)PS::field_bytes, bar);
 }
 
 // One group of L lines from the staging buffer (its copy has landed); issues
@@ -551,8 +563,8 @@ __device__ __forceinline__ void p3_tma_body(Geo g, const typename CT<real>::t *_
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N + twt_size(N, MAXR);
     cplx *stage = reinterpret_cast<cplx *>(smem_raw + PS::off);
-    load_twiddles<real>(tw, twg, N);
-    build_twt<cplx, N, MAXR>(tw + N, twg);
+    load_twiddles<real>(tw, twg, N, g.chk());
+    build_twt<cplx, N, MAXR>(tw + N, twg, g.chk());
     if (threadIdx.x == 0) mbar_init(&bar, 1);
     __syncthreads();
     long long grp = blockIdx.x;
@@ -598,8 +610,8 @@ __device__ __forceinline__ void p3_bulk_body(Geo g, const typename CT<real>::t *
         mbar_init(&bar, 1);
         p3_issue<real, N, L>(g, B, stage, &bar, grp);
     }
-    load_twiddles<real>(tw, twg, N);
-    build_twt<cplx, N, MAXR>(tw + N, twg);
+    load_twiddles<real>(tw, twg, N, g.chk());
+    build_twt<cplx, N, MAXR>(tw + N, twg, g.chk());
     if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
     __syncthreads();
     if (!s_ok) {
@@ -646,9 +658,9 @@ __device__ __forceinline__ void p3_bulkf_body(Geo g, const typename CT<real>::t 
         mbar_init(&bar, 1);
         p3_issue<real, N, L>(g, B, stage, &bar, grp);
     }
-    load_twiddles<real>(tw, twg, N);
-    build_twt<cplx, N, MAXR>(tw + N, twg);
-    build_twt<cplx, N, MAXR, true>(tw + N + twt_size(N, MAXR), twg);
+    load_twiddles<real>(tw, twg, N, g.chk());
+    build_twt<cplx, N, MAXR>(tw + N, twg, g.chk());
+    build_twt<cplx, N, MAXR, true>(tw + N + twt_size(N, MAXR), twg, g.chk());
     if (threadIdx.x == 0) s_ok = mbar_wait_bounded(&bar, 0) ? 1 : 0;
     __syncthreads();
     if (!s_ok) {
@@ -720,7 +732,7 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
+    load_twiddles<real>(tw, twg, N, g.chk());
     constexpr int Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const long long line0 = (long long)blockIdx.x * L;  // one box per launch
     const long long N3 = (long long)N * N * N;
@@ -728,8 +740,8 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
     for (int e = threadIdx.x; e < 2 * L * N; e += T) {
         const int z = e % N, pc = e / N, p = pc / L, c = pc % L;
         const long long off = (line0 + c) * N + z;
-        if (p == 0) tile[z * LD + c] = cmk<cplx>((double)u[off], (double)u[N3 + off]);
-        else tile[z * LD + L + c] = cmk<cplx>((double)u[2 * N3 + off], 0.0);
+        if (p == 0) tile[z * LD + c] = cmk<cplx>((double)DNS_LD(g, u + off), (double)DNS_LD(g, u + N3 + off));
+        else tile[z * LD + L + c] = cmk<cplx>((double)DNS_LD(g, u + 2 * N3 + off), 0.0);
     }
     __syncthreads();
     auto tload = [&](int n, int c) -> cplx { return tile[n * LD + c]; };
@@ -741,9 +753,9 @@ __global__ void __launch_bounds__(T) k_zfwd_real(Geo g, const typename CT<real>:
         const cplx zm = tile[((N - kz) % N) * LD + c];
         const cplx zb = tile[kz * LD + L + c];
         const long long off = (line0 + c) * Kzp + kz;
-        B[off] = cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y));
-        B[sB + off] = cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x));
-        B[2 * sB + off] = zb;
+        DNS_ST(g, B + off, cmk<cplx>(0.5 * (za.x + zm.x), 0.5 * (za.y - zm.y)));
+        DNS_ST(g, B + sB + off, cmk<cplx>(0.5 * (za.y + zm.y), -0.5 * (za.x - zm.x)));
+        DNS_ST(g, B + 2 * sB + off, zb);
     }
 }
 
@@ -762,8 +774,8 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
     constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const cplx *src = B + box * GeoN<N>::bB + f * GeoN<N>::sB + (long long)x * N * Kzp;
     cplx *dst = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)x * Kx * Kzp;
-    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, Kzp, N, min(W, Kzp - kz0), &bar);
-    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) rows_issue<cplx, W>(g, tile, src + kz0, Kzp, N, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N, g.chk());
     if constexpr (BULK) {
         if (!rows_wait(&bar, &s_ok, g.err)) return;
     } else {
@@ -772,12 +784,12 @@ __global__ void __launch_bounds__(T) k_p4_yfwd(Geo g, const typename CT<real>::t
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
-        return BULK ? tile[n * W + c] : src[(long long)n * Kzp + kz];
+        return BULK ? tile[n * W + c] : DNS_LD(g, src + (long long)n * Kzp + kz);
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
         const int iy = row_to_compact<N>(n, K);
-        if (kz < Kz && iy >= 0) dst[(long long)iy * Kzp + kz] = v;
+        if (kz < Kz && iy >= 0) DNS_ST(g, dst + (long long)iy * Kzp + kz, v);
     };
     TileFFT<real, N, W, T, -1, MAXR>::run(tile, W, tw, load, store);
 }
@@ -795,7 +807,7 @@ __device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real,
     typedef typename CT<real>::t cplx;
     typedef typename CT<acc>::t cacc;
     if (a.stage < 0) {
-        a.dU[e] = cmk<cacc>((acc)du.x, (acc)du.y);
+        DNS_ST(a, a.dU + e, cmk<cacc>((acc)du.x, (acc)du.y));
         return du;
     }
     const acc dx = (acc)du.x, dy = (acc)du.y;
@@ -805,13 +817,13 @@ __device__ __forceinline__ typename CT<real>::t rk_update(const UpdateArgs<real,
     u1.y += adt * dy;
     cplx next;
     if (a.stage < 3) {
-        a.U1[e] = u1;
+        DNS_ST(a, a.U1 + e, u1);
         next = cmk<cplx>((double)(u0.x + bdt * dx), (double)(u0.y + bdt * dy));
-        a.Uout[e] = next;
+        DNS_ST(a, a.Uout + e, next);
     } else {
-        a.U0out[e] = u1;
+        DNS_ST(a, a.U0out + e, u1);
         next = cmk<cplx>((double)u1.x, (double)u1.y);
-        if (a.Uout) a.Uout[e] = next;
+        if (a.Uout) DNS_ST(a, a.Uout + e, next);
     }
     return next;
 }
@@ -852,11 +864,11 @@ __device__ __forceinline__ typename CT<real>::t rk_update_if(const UpdateArgs<re
         next = cmk<cplx>((double)u1.x, (double)u1.y);
     }
     if (a.stage < 3) {
-        a.U1[e] = u1;
-        a.Uout[e] = next;
+        DNS_ST(a, a.U1 + e, u1);
+        DNS_ST(a, a.Uout + e, next);
     } else {
-        a.U0out[e] = u1;
-        if (a.Uout) a.Uout[e] = next;
+        DNS_ST(a, a.U0out + e, u1);
+        if (a.Uout) DNS_ST(a, a.Uout + e, next);
     }
     return next;
 }
@@ -877,8 +889,8 @@ __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::
     constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
     const cplx *src = A + box * GeoN<N>::bA + f * GeoN<N>::sA + (long long)jy * Kzp;
     cplx *dst = Nh + box * GeoN<N>::bB + f * GeoN<N>::sS + (long long)jy * Kzp;
-    if constexpr (BULK) rows_issue<cplx, W>(tile, src + kz0, (long long)Kx * Kzp, N, min(W, Kzp - kz0), &bar);
-    load_twiddles<real>(tw, twg, N);
+    if constexpr (BULK) rows_issue<cplx, W>(g, tile, src + kz0, (long long)Kx * Kzp, N, min(W, Kzp - kz0), &bar);
+    load_twiddles<real>(tw, twg, N, g.chk());
     if constexpr (BULK) {
         if (!rows_wait(&bar, &s_ok, g.err)) return;
     } else {
@@ -887,12 +899,12 @@ __global__ void __launch_bounds__(T) k_p5a_xfwd(Geo g, const typename CT<real>::
     auto load = [&](int n, int c) -> cplx {
         const int kz = kz0 + c;
         if (kz >= Kz) return cmk<cplx>(0.0, 0.0);
-        return BULK ? tile[n * W + c] : src[(long long)n * Kx * Kzp + kz];
+        return BULK ? tile[n * W + c] : DNS_LD(g, src + (long long)n * Kx * Kzp + kz);
     };
     auto store = [&](int n, int c, cplx v) {
         const int kz = kz0 + c;
         const int ix = row_to_compact<N>(n, K);
-        if (kz < Kz && ix >= 0) dst[(long long)ix * Kx * Kzp + kz] = v;
+        if (kz < Kz && ix >= 0) DNS_ST(g, dst + (long long)ix * Kx * Kzp + kz, v);
     };
     TileFFT<real, N, W, T, -1, MAXR>::run(tile, W, tw, load, store);
 }
@@ -912,17 +924,18 @@ __device__ __forceinline__ void p5_mode_update(const UpdateArgs<real, acc> &args
     typedef GeoN<N> G;
     constexpr long long sS = G::sS;
     const long long m = box * G::bS + ((long long)ix * G::Kx + iy) * G::Kzp + kz;  // state element, component 0
-    const real nu = (real)(args.nu_box ? args.nu_box[box] : args.nu);
+    const real nu = (real)(args.nu_box ? DNS_LD(args, args.nu_box + box) : args.nu);
     if (args.Fext && args.stage != -2) {
-        const cplx f0 = args.Fext[m], f1 = args.Fext[sS + m], f2 = args.Fext[2 * sS + m];
+        const cplx f0 = DNS_LD(args, args.Fext + m), f1 = DNS_LD(args, args.Fext + sS + m),
+                   f2 = DNS_LD(args, args.Fext + 2 * sS + m);
         n0 = cadd(n0, f0);
         n1 = cadd(n1, f1);
         n2 = cadd(n2, f2);
     }
     if (args.stage == -2) {  // bare forward transform (physical input)
-        args.dU[m] = cmk<cacc>(n0.x, n0.y);
-        args.dU[sS + m] = cmk<cacc>(n1.x, n1.y);
-        args.dU[2 * sS + m] = cmk<cacc>(n2.x, n2.y);
+        DNS_ST(args, args.dU + m, cmk<cacc>(n0.x, n0.y));
+        DNS_ST(args, args.dU + sS + m, cmk<cacc>(n1.x, n1.y));
+        DNS_ST(args, args.dU + 2 * sS + m, cmk<cacc>(n2.x, n2.y));
         return;
     }
     // every load of the mode before any store (the output arrays may alias
@@ -934,9 +947,9 @@ __device__ __forceinline__ void p5_mode_update(const UpdateArgs<real, acc> &args
     for (int c = 0; c < 3; ++c) {
         v[c] = cmk<cplx>(0.0, 0.0);
         s0[c] = s1[c] = cmk<cacc>(0.0, 0.0);
-        if (!ifrk) v[c] = args.U[c * sS + m];
-        if (args.stage >= 0 && args.stage < 3) s0[c] = args.U0[c * sS + m];
-        if (args.stage > 0) s1[c] = args.U1[c * sS + m];
+        if (!ifrk) v[c] = DNS_LD(args, args.U + c * sS + m);
+        if (args.stage >= 0 && args.stage < 3) s0[c] = DNS_LD(args, args.U0 + c * sS + m);
+        if (args.stage > 0) s1[c] = DNS_LD(args, args.U1 + c * sS + m);
     }
     const real kx = (real)compact_to_k(ix, G::K), ky = (real)compact_to_k(iy, G::K), kzr = (real)kz;
     const real k2 = kx * kx + ky * ky + kzr * kzr;
@@ -968,9 +981,9 @@ __device__ __forceinline__ void p5_mode_update(const UpdateArgs<real, acc> &args
     if (args.stage >= 0 && args.Om) {  // curl of the next stage input for the next P1
         cplx ox, oy, oz;
         curl_mode<cplx, real>(kx, ky, kzr, x0, x1, x2, ox, oy, oz);
-        args.Om[m] = ox;
-        args.Om[sS + m] = oy;
-        args.Om[2 * sS + m] = oz;
+        DNS_ST(args, args.Om + m, ox);
+        DNS_ST(args, args.Om + sS + m, oy);
+        DNS_ST(args, args.Om + 2 * sS + m, oz);
     }
 }
 
@@ -988,7 +1001,7 @@ __global__ void k_p5b_update(const typename CT<real>::t *__restrict__ Nh, Update
     const int r = mm / G::Kzp;
     const int iy = r % G::Kx, ix = r / G::Kx;
     const long long nm = box * G::bB + mm;  // N^ lives in B, state layout
-    const cplx n0 = Nh[nm], n1 = Nh[G::sS + nm], n2 = Nh[2 * G::sS + nm];
+    const cplx n0 = DNS_LD(args, Nh + nm), n1 = DNS_LD(args, Nh + G::sS + nm), n2 = DNS_LD(args, Nh + 2 * G::sS + nm);
     p5_mode_update<real, acc, N>(args, box, ix, iy, kz, n0, n1, n2);
 }
 
@@ -1005,7 +1018,7 @@ __global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::
     extern __shared__ __align__(16) unsigned char smem_raw[];
     cplx *tw = reinterpret_cast<cplx *>(smem_raw);
     cplx *tile = tw + N;
-    load_twiddles<real>(tw, twg, N);
+    load_twiddles<real>(tw, twg, N, g.chk());
     __syncthreads();
     const int box = blockIdx.x, kz0 = blockIdx.y * W, jy = blockIdx.z;
     constexpr int K = GeoN<N>::K, Kx = GeoN<N>::Kx, Kz = GeoN<N>::Kz, Kzp = GeoN<N>::Kzp;
@@ -1013,7 +1026,7 @@ __global__ void __launch_bounds__(T) k_p5_fused(Geo g, const typename CT<real>::
     auto load = [&](int n, int c) -> cplx {
         const int f = c / W, cc = c % W;
         if (kz0 + cc >= Kz) return cmk<cplx>(0.0, 0.0);
-        return src[f * GeoN<N>::sA + (long long)n * Kx * Kzp + cc];
+        return DNS_LD(g, src + f * GeoN<N>::sA + (long long)n * Kx * Kzp + cc);
     };
     auto tstore = [&](int n, int c, cplx v) { tile[n * WT + c] = v; };
     TileFFT<real, N, WT, T, -1, MAXR>::run(tile, WT, tw, load, tstore);
@@ -1043,16 +1056,16 @@ __global__ void k_full_to_compact(Geo g, const Tin *__restrict__ full, Tout *__r
     const Tin *src = full + (((long long)c * N + fx) * N + fy) * Nh;
     const long long o = c * g.sS + ((long long)ix * Kx + iy) * Kzp;
     for (int kz = threadIdx.x; kz < Kz; kz += blockDim.x) {
-        const Tin v = src[kz];
+        const Tin v = DNS_LD(g, src + kz);
         Tout a;
         a.x = v.x;
         a.y = v.y;
-        cmp[o + kz] = a;
+        DNS_ST(g, cmp + o + kz, a);
         if (cmp2) {
             Tout2 b;
             b.x = v.x;
             b.y = v.y;
-            cmp2[o + kz] = b;
+            DNS_ST(g, cmp2 + o + kz, b);
         }
     }
 }
@@ -1071,11 +1084,11 @@ __global__ void k_compact_to_full(Geo g, const Tin *__restrict__ cmp, Tout *__re
         o.x = 0;
         o.y = 0;
         if (kept && kz <= K) {
-            const Tin v = src[kz];
+            const Tin v = DNS_LD(g, src + kz);
             o.x = v.x;
             o.y = v.y;
         }
-        dst[kz] = o;
+        DNS_ST(g, dst + kz, o);
     }
 }
 
@@ -1097,7 +1110,7 @@ __global__ void k_energy_partials(Geo g, const typename CT<acc>::t *__restrict__
         const long long m = ((long long)ix * Kx + iy) * Kzp + kz;
         double p = 0.0;
         for (int c = 0; c < 3; ++c) {
-            const typename CT<acc>::t v = U[c * g.sS + m];
+            const typename CT<acc>::t v = DNS_LD(g, U + c * g.sS + m);
             p += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
         }
         const double w = kz == 0 ? 1.0 : 2.0;
@@ -1121,8 +1134,8 @@ __global__ void k_energy_partials(Geo g, const typename CT<acc>::t *__restrict__
             a += rs[0][w];
             b += rs[1][w];
         }
-        partials[2 * blockIdx.x] = a;
-        partials[2 * blockIdx.x + 1] = b;
+        DNS_ST(g, partials + 2 * blockIdx.x, a);
+        DNS_ST(g, partials + 2 * blockIdx.x + 1, b);
     }
 }
 
@@ -1165,7 +1178,7 @@ __global__ void k_spectrum(Geo g, const typename CT<acc>::t *__restrict__ U, dou
         for (int kz = a; kz < b; ++kz) {
             double p = 0.0;
             for (int c = 0; c < 3; ++c) {
-                const typename CT<acc>::t v = U[c * g.sS + m0 + kz];
+                const typename CT<acc>::t v = DNS_LD(g, U + c * g.sS + m0 + kz);
                 p += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
             }
             acc_s += (kz == 0 ? 1.0 : 2.0) * p;
@@ -1179,7 +1192,7 @@ __global__ void k_spectrum(Geo g, const typename CT<acc>::t *__restrict__ U, dou
         double t = 0.0;
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += rs[w];
         const double N3 = (double)g.N * g.N * g.N;
-        Ek[s] = t / (2.0 * N3 * N3);
+        DNS_ST(g, Ek + s, t / (2.0 * N3 * N3));
     }
 }
 

@@ -82,7 +82,7 @@ __device__ __forceinline__ void zw_twiddle_all(float2 *v, const float2 (&wa)[NA]
 // classified at compile time: all kept, none kept, or decided per lane.
 template <int N, int K1>
 __device__ __forceinline__ float2 zw_load(const float2 *__restrict__ fa, const float2 *__restrict__ fb, int k2,
-                                          float bscale) {
+                                          float bscale, const Chk &ck) {
     constexpr int K = GeoN<N>::K;
     constexpr int lo = 16 * K1, hi = 16 * K1 + 15;
     // kz(n) = n for n <= N/2, N - n above; kept iff kz <= K
@@ -96,7 +96,7 @@ __device__ __forceinline__ float2 zw_load(const float2 *__restrict__ fa, const f
         const bool low = all_low || (!all_high && n <= N / 2);
         const int kz = low ? n : N - n;
         if (!(all_low || all_high) && kz > K) return make_float2(0.f, 0.f);
-        float2 a = fa[kz], b = fb[kz];
+        float2 a = DNS_LD(ck, fa + kz), b = DNS_LD(ck, fb + kz);
         if (K1 == 0 && n == 0) {  // Im of X[0] is ignored by the real inverse
             a.y = 0.f;
             b.y = 0.f;
@@ -108,10 +108,11 @@ __device__ __forceinline__ float2 zw_load(const float2 *__restrict__ fa, const f
 }
 
 template <int N, int N1, int K1 = 0>
-__device__ __forceinline__ void zw_load_all(float2 *v, const float2 *fa, const float2 *fb, int k2, float bscale) {
+__device__ __forceinline__ void zw_load_all(float2 *v, const float2 *fa, const float2 *fb, int k2, float bscale,
+                                            const Chk &ck) {
     if constexpr (K1 < N1) {
-        v[K1] = zw_load<N, K1>(fa, fb, k2, bscale);
-        zw_load_all<N, N1, K1 + 1>(v, fa, fb, k2, bscale);
+        v[K1] = zw_load<N, K1>(fa, fb, k2, bscale, ck);
+        zw_load_all<N, N1, K1 + 1>(v, fa, fb, k2, bscale, ck);
     }
 }
 
@@ -119,7 +120,7 @@ __device__ __forceinline__ void zw_load_all(float2 *v, const float2 *fa, const f
 // Nx + i Ny (unpacked with Z[N - k] from the partner lane), f = 1 is Nz.
 template <int N, int N1, int K1 = 0>
 __device__ __forceinline__ void zw_store_all(const float2 *v, int k2, int lane, int f, float2 *__restrict__ dst,
-                                             long long sB) {
+                                             long long sB, const Chk &ck) {
     constexpr int K = GeoN<N>::K;
     if constexpr (16 * K1 <= K) {
         // Z[N - k]: k2 > 0 -> lane 16 - k2 of this half-warp, entry N1 - 1 - K1;
@@ -133,13 +134,13 @@ __device__ __forceinline__ void zw_store_all(const float2 *v, int k2, int lane, 
         if (kz <= K) {
             const float2 za = v[K1];
             if (f == 0) {
-                dst[kz] = make_float2(0.5f * (za.x + zm.x), 0.5f * (za.y - zm.y));
-                dst[sB + kz] = make_float2(0.5f * (za.y + zm.y), -0.5f * (za.x - zm.x));
+                DNS_ST(ck, dst + kz, make_float2(0.5f * (za.x + zm.x), 0.5f * (za.y - zm.y)));
+                DNS_ST(ck, dst + sB + kz, make_float2(0.5f * (za.y + zm.y), -0.5f * (za.x - zm.x)));
             } else {
-                dst[2 * sB + kz] = za;
+                DNS_ST(ck, dst + 2 * sB + kz, za);
             }
         }
-        zw_store_all<N, N1, K1 + 1>(v, k2, lane, f, dst, sB);
+        zw_store_all<N, N1, K1 + 1>(v, k2, lane, f, dst, sB, ck);
     }
 }
 
@@ -158,9 +159,9 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_p3_zwarp(Geo g, const float2
     wb[0] = make_float2(1.f, 0.f);
     wa[0] = make_float2(1.f, 0.f);
 #pragma unroll
-    for (int b = 1; b < 8; ++b) wb[b] = twg[(k2 * b) % N];
+    for (int b = 1; b < 8; ++b) wb[b] = DNS_LD(g, twg + (k2 * b) % N);
 #pragma unroll
-    for (int a = 1; a < NA; ++a) wa[a] = twg[(8 * k2 * a) % N];
+    for (int a = 1; a < NA; ++a) wa[a] = DNS_LD(g, twg + (8 * k2 * a) % N);
 
     const long long nw = (long long)gridDim.x * WPB;
     for (long long u = (long long)blockIdx.x * WPB + warp; u < nunits; u += nw) {
@@ -177,7 +178,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_p3_zwarp(Geo g, const float2
                 const float2 *fa = Bb + P3Pairs<N>::fa(p) * sB + ln * Kzp;
                 const float2 *fb = Bb + P3Pairs<N>::fb(p) * sB + ln * Kzp;
                 float2 v[N1];
-                zw_load_all<N, N1>(v, fa, fb, k2, p == 1 ? (float)(1.0 / P3Pairs<N>::S) : 1.f);
+                zw_load_all<N, N1>(v, fa, fb, k2, p == 1 ? (float)(1.0 / P3Pairs<N>::S) : 1.f, g.chk());
                 dft<N1, +1>(v);
                 zw_twiddle_all<N, N1, NA>(v, wa, wb, true);
                 float2 *dst = buf + pl * N1 * P1 + k2;
@@ -236,7 +237,7 @@ __global__ void __launch_bounds__(32 * WPB, MINB) k_p3_zwarp(Geo g, const float2
             for (int n1 = 0; n1 < N1; ++n1) v[n1] = src[n1];
             zw_twiddle_all<N, N1, NA>(v, wa, wb, false);
             dft<N1, -1>(v);
-            zw_store_all<N, N1>(v, k2, lane, f, Bb + ln * Kzp, sB);
+            zw_store_all<N, N1>(v, k2, lane, f, Bb + ln * Kzp, sB, g.chk());
         }
         __syncwarp();  // the buffer is free for the next unit
     }

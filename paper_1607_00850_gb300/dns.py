@@ -16,11 +16,14 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libdns.so")
+# the index-checked build (build.build(checked=True)); load() takes it when
+# the environment sets DNS_CHECKED=1
+LIB_CHECKED_PATH = os.path.join(_HERE, "libdns_checked.so")
 
 DNS_F32, DNS_F64, DNS_F32_ACC64 = 0, 1, 2
 DTYPE_NAMES = {"f32": DNS_F32, "f64": DNS_F64, "f32_acc64": DNS_F32_ACC64}
 STATUS = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_OOM", 3: "DNS_ERR_CUDA", 4: "DNS_ERR_TIMEOUT",
-          5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED", 7: "DNS_ERR_GUARD"}
+          5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED", 7: "DNS_ERR_GUARD", 8: "DNS_ERR_INDEX"}
 SUPPORTED_N = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 128, 144, 192, 256, 288, 384, 512, 576, 768, 1024)
 
 # symbol -> (restype, argtypes); the complete exported surface of dns.h
@@ -83,6 +86,9 @@ SIGNATURES = {
     "dns_fp64_fma_rate": (_i, [_d, _dp]),
     "dns_strerror": (ctypes.c_char_p, [_i]),
     "dns_last_cuda_error": (ctypes.c_char_p, []),
+    "dns_checked_build": (_i, []),
+    "dns_first_bad_access": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(ctypes.c_ulonglong)]),
+    "dns_check_index_selftest": (_i, [_vp]),
 }
 
 
@@ -95,11 +101,14 @@ class DnsError(RuntimeError):
 _LIB = None
 
 
-def load(path: str = LIB_PATH):
-    """Load libdns.so and declare every entry point; raises if it is missing."""
+def load(path: str | None = None):
+    """Load libdns.so (libdns_checked.so if DNS_CHECKED=1 is set) and declare
+    every entry point; raises if it is missing."""
     global _LIB
     if _LIB is not None:
         return _LIB
+    if path is None:
+        path = LIB_CHECKED_PATH if os.environ.get("DNS_CHECKED") == "1" else LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"{path} is not built; run __graft_entry__.build() (needs nvcc). "
                            "There is no CPU fallback.")
@@ -658,3 +667,20 @@ def dns_les_set_closure_stages(h: int, every_stage: bool) -> None:
 
 def dns_net_set_closure_scaling(net: int, in_scale: float, out_scale: float) -> None:
     _check(load().dns_net_set_closure_scaling(net, float(in_scale), float(out_scale)), "dns_net_set_closure_scaling")
+
+
+def dns_checked_build() -> bool:
+    """True when the loaded library is the index-checked build."""
+    return bool(load().dns_checked_build())
+
+
+def dns_first_bad_access(h: int):
+    """(source line, address) of the first access an index-checked kernel
+    rejected on this handle, or (0, 0)."""
+    line, addr = ctypes.c_int(), ctypes.c_ulonglong()
+    _check(load().dns_first_bad_access(h, ctypes.byref(line), ctypes.byref(addr)), "dns_first_bad_access")
+    return line.value, addr.value
+
+
+def dns_check_index_selftest(h: int) -> None:
+    _check(load().dns_check_index_selftest(h), "dns_check_index_selftest")

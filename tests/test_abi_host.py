@@ -73,9 +73,30 @@ def test_null_handle_is_rejected(lib):
 
 def test_status_strings(lib):
     from paper_1607_00850_gb300 import dns
-    for code in range(8):
+    for code in range(9):
         assert dns.dns_strerror(code) != "unknown status"
     assert dns.dns_strerror(99) == "unknown status"
+
+
+def test_checked_build_entry_points_in_the_plain_library(lib):
+    # the production library is not the checked build: its self-test is
+    # unsupported, and both calls reject a null handle first
+    assert lib.dns_checked_build() == 0
+    assert lib.dns_check_index_selftest(None) == 1
+    line, addr = ctypes.c_int(), ctypes.c_ulonglong()
+    assert lib.dns_first_bad_access(None, ctypes.byref(line), ctypes.byref(addr)) == 1
+
+
+def test_checked_library_builds_and_exports_the_same_boundary():
+    # libdns_checked.so (-DDNS_CHECKED): every declared entry point, and it
+    # says it is the checked build (no CUDA call is made here)
+    from paper_1607_00850_gb300 import build
+    path = build.build(checked=True)
+    chk = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(chk, s), s
+    assert chk.dns_checked_build() == 1
+    assert set(build.CHECKED_SIZES) <= set(build.SIZES)
 
 
 def test_supported_sizes_match_plan():
