@@ -61,7 +61,9 @@ def config(N, dt):
             "l2": "inputs larger than L2 (working set several GB); no flush"}
 
 
-KERNEL_SOURCES = ("dns_fft.cuh", "dns_async.cuh", "dns_passes.cuh", "dns_zwarp.cuh", "dns_launch.cuh", "dns_inst.cu")
+KERNEL_SOURCES = ("dns_fft.cuh", "dns_async.cuh", "dns_check.cuh", "dns_passes.cuh", "dns_zwarp.cuh", "dns_zwarp1k.cuh",
+                  "dns_launch.cuh",
+                  "dns_inst.cu")
 
 
 def kernel_source_hash():

@@ -15,6 +15,7 @@
 #include "dns_internal.h"
 #include "dns_passes.cuh"
 #include "dns_zwarp.cuh"
+#include "dns_zwarp1k.cuh"
 
 namespace dns {
 
@@ -328,35 +329,43 @@ template <typename real, int N, int V> static void fill_col(PassSet *ps) {
     }
 }
 
-// Warp-per-line z pass (dns_zwarp.cuh): FP32, N = 256 and 512, persistent
-// blocks of WPB warps; the two variants differ in the register cap (MINB
-// blocks resident per SM).  They take the last two P3 variant slots.
+// Warp-per-line z pass (dns_zwarp.cuh, N = 256 and 512; dns_zwarp1k.cuh,
+// N = 1024): FP32, persistent blocks of WPB warps, in the last two P3
+// variant slots.  At 256 and 512 they differ in the register cap (MINB
+// blocks resident per SM); at 1024 (26 KB of shared memory per warp, so at
+// most 8 warps per SM) in the block size: 4 warps x 2 blocks or 8 x 1.
 template <int N, int V> struct ZWShape {
-    static constexpr int WPB = 4;
-    static constexpr int MINB = V == PassSet::NP3V - 2 ? 4 : 3;
+    static constexpr bool K1024 = N == 1024;
+    static constexpr int WPB = K1024 ? (V == PassSet::NP3V - 2 ? 4 : 8) : 4;
+    static constexpr int MINB = K1024 ? (V == PassSet::NP3V - 2 ? 2 : 1) : (V == PassSet::NP3V - 2 ? 4 : 3);
     static constexpr int T = 32 * WPB;
-    static constexpr bool valid = (N == 256 || N == 512);
+    static constexpr bool valid = (N == 256 || N == 512 || N == 1024);
+    static constexpr int LW = K1024 ? 1 : ZW<(K1024 ? 512 : N)>::LW;   // lines per warp unit
+    static constexpr int N1 = K1024 ? 64 : N / 16;
+    static constexpr size_t SMEM = K1024 ? ZW1k::smem(WPB) : ZW<(K1024 ? 512 : N)>::smem(WPB);
 };
 
 template <int N, int V> struct ZWLaunch {
     typedef ZWShape<N, V> S;
     static inline int resident = 0;  // persistent grid: SMs x blocks per SM (set by prepare)
-    static auto kernel() { return k_p3_zwarp<N, S::WPB, S::MINB>; }
+    static auto kernel() {
+        if constexpr (N == 1024) return k_p3_zwarp1k<S::WPB, S::MINB>;
+        else return k_p3_zwarp<N, S::WPB, S::MINB>;
+    }
     static cudaError_t p3(const Geo &g, const void *tw, void *B, cudaStream_t st) {
         if (g.Kzp != GeoN<N>::Kzp || resident < 1 || g.nb < 1) return cudaErrorInvalidValue;
-        const long long units = (long long)N * N / ZW<N>::LW * g.nb;
+        const long long units = (long long)N * N / S::LW * g.nb;
         const long long blocks = (units + S::WPB - 1) / S::WPB;
         const unsigned grid = (unsigned)(blocks < resident ? blocks : resident);
-        kernel()<<<grid, S::T, ZW<N>::smem(S::WPB), st>>>(g, (const float2 *)tw, (float2 *)B, units);
+        kernel()<<<grid, S::T, S::SMEM, st>>>(g, (const float2 *)tw, (float2 *)B, units);
         return cudaGetLastError();
     }
     static cudaError_t prepare() {
-        cudaError_t e = set_smem(kernel(), ZW<N>::smem(S::WPB));
+        cudaError_t e = set_smem(kernel(), S::SMEM);
         int dev = 0, sms = 0, occ = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel(), S::T, ZW<N>::smem(S::WPB));
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel(), S::T, S::SMEM);
         if (e == cudaSuccess) resident = sms * (occ > 0 ? occ : 1);
         return e;
     }
@@ -367,8 +376,8 @@ template <typename real, int N, int V> static void fill_p3(PassSet *ps) {
         if constexpr (sizeof(real) == 4 && ZWShape<N, V>::valid) {
             ps->p3[V] = ZWLaunch<N, V>::p3;
             ps->prep_p3[V] = ZWLaunch<N, V>::prepare;
-            ps->p3_l[V] = ZW<N>::LW;
-            ps->p3_r[V] = ZW<N>::N1;
+            ps->p3_l[V] = ZWShape<N, V>::LW;
+            ps->p3_r[V] = ZWShape<N, V>::N1;
             ps->p3_t[V] = ZWShape<N, V>::T;
         }
         fill_p3<real, N, V + 1>(ps);

@@ -444,3 +444,80 @@ def test_bad_arguments_on_live_handle(dns):
         q = dns.dns_query(s.h)
         assert q["N"] == 16 and q["kmax"] == 5 and q["dtype"] == 0
         assert dns.dns_device_bytes(s.h) > 0
+
+
+@pytest.mark.slow
+def test_rhs_1024_every_z_variant(dns, orc):
+    # Every compiled z-pass variant at 1024^3 (the warp-per-line kernels of
+    # the last slots included), FP32, two ways the oracle can anchor at this
+    # size:
+    # (1) a random 512^3 field embedded in the 1024^3 spectrum (coefficients
+    #     times 8 = (1024/512)^3, the same physical field): its products reach
+    #     |k_i| <= 340 <= K, so the 1024^3 right-hand side on |k_i| <= 170 is
+    #     8 times the 512^3 oracle's (which aliases only onto modes its 2/3
+    #     rule discards), compared mode by mode;
+    # (2) a solenoidal field with unit-variance modes on the whole kept cube,
+    #     made on the device: the right-hand side is solenoidal and its
+    #     nonlinear part moves no energy (as in test_rhs_1024_random_invariants).
+    N, M, nu = 1024, 512, 1.0 / 4000
+    Km, K = (M - 1) // 3, (N - 1) // 3
+    small = inputs.random_isotropic(M, seed=79, k0=4.0)
+    ref = orc.rhs(small, nu)
+    idx = torch.cat([torch.arange(0, Km + 1), torch.arange(-Km, 0)])
+    im, ig = idx % M, (idx % N).cuda()
+    xe = torch.zeros((3, N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+    xe[:, ig[:, None], ig[None, :], : Km + 1] = (8.0 * torch.from_numpy(small)[:, im[:, None], im[None, :], : Km + 1]
+                                                 ).to(torch.complex64).cuda()
+    refd = torch.from_numpy(ref[:, im[:, None], im[None, :], : Km + 1]).cuda()
+    del small, ref
+    # full-spectrum solenoidal field on the kept cube
+    gen = torch.Generator(device="cuda").manual_seed(1024)
+    k1 = torch.fft.fftfreq(N, 1.0 / N, device="cuda", dtype=torch.float64)
+    kz = torch.arange(N // 2 + 1, device="cuda", dtype=torch.float64)
+    xf = torch.zeros_like(xe)
+    for i in range(N):
+        if abs(k1[i]) > K:
+            continue
+        u = torch.randn((3, N, N // 2 + 1), generator=gen, device="cuda", dtype=torch.float64) + 1j * torch.randn(
+            (3, N, N // 2 + 1), generator=gen, device="cuda", dtype=torch.float64)
+        kv = torch.stack(torch.broadcast_tensors(k1[i] + 0 * k1[:, None] + 0 * kz[None, :], k1[:, None] + 0 * kz[None, :],
+                                                 kz[None, :] + 0 * k1[:, None]))
+        k2 = (kv ** 2).sum(0)
+        k2[k2 == 0] = 1.0
+        u = u - kv * (kv * u).sum(0) / k2
+        keep = (k1[:, None].abs() <= K) & (kz[None, :] <= K)
+        u = u * keep
+        u[:, :, 0] = 0.0  # kz = 0 plane left empty: no Hermitian pairing needed
+        xf[:, i] = u.to(torch.complex64)
+    w = torch.full_like(kz, 2.0)
+    w[0] = w[-1] = 1.0
+    checked = 0
+    with dns.Solver(N, nu, 1e-3, dns.DNS_F32) as s:
+        for v in range(32):
+            if dns.dns_variant_info(s.h, 2, v) is None:
+                continue
+            dns.dns_set_plan(s.h, [0, 0, v, 0, 0])
+            y = torch.empty_like(xe)
+            torch.cuda.synchronize()
+            s.rhs(xe, y)
+            got = y[:, ig[:, None], ig[None, :], : Km + 1].to(torch.complex128) / 8.0
+            for c in range(3):
+                err, scale = float((got[c] - refd[c]).abs().max()), float(refd[c].abs().max())
+                assert err <= 2e-6 * scale, f"variant {v} component {c}: {err:.3e} vs {scale:.3e}"
+            del got
+            s.rhs(xf, y)
+            div, dmag, rate, visc, scale = 0.0, 0.0, 0.0, 0.0, 0.0
+            for i in range(N):
+                u, d = xf[:, i].to(torch.complex128), y[:, i].to(torch.complex128)
+                kd = k1[i] * d[0] + k1[:, None] * d[1] + kz[None, :] * d[2]
+                k2 = k1[i] ** 2 + k1[:, None] ** 2 + kz[None, :] ** 2
+                div = max(div, float(kd.abs().max()))
+                dmag = max(dmag, float((k2.sqrt() * d.abs().amax(0)).max()))
+                rate += float((w * (u.conj() * d).real.sum(0)).sum())
+                visc += float((w * k2 * (u.abs() ** 2).sum(0)).sum())
+                scale += float((w * (u.abs() * d.abs()).sum(0)).sum())
+            assert div < 1e-5 * dmag, f"variant {v}: divergence {div:.3e} vs {dmag:.3e}"
+            assert abs(rate + nu * visc) < 1e-5 * scale, f"variant {v}: energy {rate + nu * visc:.3e} vs {scale:.3e}"
+            checked += 1
+            del y
+    assert checked >= 3
