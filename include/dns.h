@@ -173,7 +173,7 @@ int dns_check_wait_timeout(dns_handle h, double seconds);
 /* Index-checked build (no counterpart in the paper; a bounds checker for
  * systems without a memory checker).  The library can also be compiled as
  * libdns_checked.so (-DDNS_CHECKED; the mesh sizes 16, 24, 36, 64, 96, 128,
- * 256 and 512 only, others return DNS_ERR_UNSUPPORTED), whose solver
+ * 256, 512 and 1024 only, others return DNS_ERR_UNSUPPORTED), whose solver
  * kernels -- every pass of the right-hand side and of the RK4 update, the
  * layout conversions, curl and diagnostics, and the source of every bulk
  * copy -- compare each global address they are about to use with the

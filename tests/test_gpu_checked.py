@@ -12,6 +12,9 @@ process with libdns.so) and runs, at every mesh the checked build compiles:
   integrating-factor RK4 step against or_rk4 / or_rk4_if;
 * an ensemble step (boxes of two sizes), device-buffer and streamed host
   I/O, physical-space input, energy, dissipation and the spectrum;
+* at 1024^3 (beyond the oracle's host memory) every variant of every pass
+  and one step on a band-limited field made on the device, for the checks
+  alone;
 
 and after each handle's work asserts that no access was rejected
 (dns_first_bad_access == (0, 0)) and that the guard regions are intact.
@@ -69,6 +72,8 @@ def _child():
 
     tol = {dns.DNS_F32: 2e-6, dns.DNS_F64: 1e-12, dns.DNS_F32_ACC64: 2e-6}
     for N in build.CHECKED_SIZES:
+        if N == 1024:
+            continue  # beyond the oracle's host memory: below, without a reference
         uh = inputs.random_box(N, seed=900 + N)
         ref = orc.rhs(uh, nu)
         dtypes = [dns.DNS_F32] + ([dns.DNS_F64, dns.DNS_F32_ACC64] if N <= 128 else [])
@@ -116,6 +121,34 @@ def _child():
             ref1 = orc.rk4_if(u0, 1e-2, dt, 1) if ifrk else orc.rk4(u0, 1e-2, dt, 1)
             compare(got, ref1, 4e-6, f"N={N} step ifrk={ifrk}")
         print(f"N={N}: steps clean", flush=True)
+
+    # 1024^3: every variant of every pass and one step on a field made on the
+    # device (a 64^3-band random field), checked for rejected accesses only
+    N = 1024
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    xb = torch.zeros((3, N, N, N // 2 + 1), dtype=torch.complex64, device="cuda")
+    xb[:, :22, :22, 1:22] = torch.randn((3, 22, 22, 21), generator=gen, device="cuda", dtype=torch.complex64)
+    yb = torch.empty_like(xb)
+    with dns.Solver(N, 1e-4, 1e-4, dns.DNS_F32) as s:
+        n_var = 0
+        for p in range(5):
+            for v in range(32):
+                if dns.dns_variant_info(s.h, p, v) is None:
+                    continue
+                plan = [0] * 5
+                plan[p] = v
+                dns.dns_set_plan(s.h, plan)
+                s.rhs(xb, yb)
+                torch.cuda.synchronize()
+                assert bool(torch.isfinite(torch.view_as_real(yb)).all()), f"N=1024 pass {p} variant {v}"
+                n_var += 1
+        clean(s.h, "N=1024 variants")
+        s.set_velocity(xb)
+        s.step(1)
+        s.synchronize()
+        clean(s.h, "N=1024 step")
+    del xb, yb
+    print(f"N=1024: {n_var} variants and a step clean", flush=True)
 
     # physical-space input and streamed host I/O
     N = 64
