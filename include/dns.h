@@ -222,7 +222,7 @@ int dns_device_bytes(dns_handle h, long long *bytes);
  * in a few launch shapes: lines per block, largest radix of the FFT plan
  * and thread count, and with its input either loaded by the threads or
  * landed in shared memory by bulk asynchronous copies.  Pass 4 also has
- * fused variants (numbers from 8 up) that transform along x and apply the
+ * fused variants (numbers from 10 up) that transform along x and apply the
  * projection, viscous term and RK4 stage in the same launch.  A "plan"
  * picks one variant per pass; variant 0 is the default.  Every variant
  * computes the same right-hand side (up to rounding order).

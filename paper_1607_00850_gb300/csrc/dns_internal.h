@@ -30,7 +30,7 @@ typedef cudaError_t (*P5Fused)(const Geo &, const void *tw, const void *A, const
 // Entry points for one (N, dtype): every compiled variant of each tuned pass
 // (nullptr where a shape is not compiled) and the untuned kernels.
 struct PassSet {
-    static constexpr int NCOLV = 8;  // column-pass variants (W, RC, input by threads or bulk copy)
+    static constexpr int NCOLV = 10;  // column-pass variants (W, RC, input by threads or bulk copy)
     static constexpr int NP3V = 16;   // z-pass variants (L, R3, resident blocks, input feed; the last two: one warp per line)
     ColP1 p1[NCOLV] = {};
     ColPass p2[NCOLV] = {}, p4[NCOLV] = {}, p5a[NCOLV] = {};

@@ -30,8 +30,8 @@ template <typename real> struct VariantTable;
 // with the inverse-last / cross / forward-first stages fused in registers.
 template <> struct VariantTable<float> {
     static constexpr int BUD = 32;
-    static constexpr int colW[4] = {16, 32, 16, 16};
-    static constexpr int colR[4] = {16, 16, 8, 32};
+    static constexpr int colW[5] = {16, 32, 16, 16, 8};
+    static constexpr int colR[5] = {16, 16, 8, 32, 32};
     static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
     static constexpr int p3R[14] = {32, 32, 32, 32, 32, 16, 32, 32, 32, 32, 32, 32, 32, 32};
     static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
@@ -39,8 +39,8 @@ template <> struct VariantTable<float> {
 };
 template <> struct VariantTable<double> {
     static constexpr int BUD = 16;
-    static constexpr int colW[4] = {8, 16, 8, 8};
-    static constexpr int colR[4] = {8, 8, 16, 32};
+    static constexpr int colW[5] = {8, 16, 8, 8, 4};
+    static constexpr int colR[5] = {8, 8, 16, 32, 32};
     static constexpr int p3S[14] = {0, 0, 1, 1, 2, 0, 0, 1, 0, 0, 1, 0, 1, 1};
     static constexpr int p3R[14] = {16, 16, 16, 16, 16, 8, 16, 16, 16, 16, 16, 16, 16, 16};
     static constexpr int p3M[14] = {1, 2, 1, 2, 2, 1, 1, 2, 1, 2, 2, 1, 1, 2};
@@ -53,12 +53,16 @@ __host__ __device__ constexpr int raw_threads(int N, int W, int BUD) {
 __host__ __device__ constexpr int at_least_32(int t) { return t < 32 ? 32 : t; }
 
 // Column variants 0..3 load their input with the threads; 4..7 are the same
-// shapes fed by bulk copies of the tile's input rows.
+// shapes fed by bulk copies of the tile's input rows; 8 and 9 are the half-
+// width shape (64-byte rows: a third of the shared memory of 128-byte rows
+// at 1024^3, so three blocks share an SM where one did) loaded by the
+// threads and by bulk copies.
 template <typename real, int N, int V> struct ColShape {
     typedef VariantTable<real> VT;
-    static constexpr int W = VT::colW[V % 4];
-    static constexpr int RC = VT::colR[V % 4];
-    static constexpr bool BULK = V >= 4;
+    static constexpr int SH = V < 8 ? V % 4 : 4;
+    static constexpr int W = VT::colW[SH];
+    static constexpr int RC = VT::colR[SH];
+    static constexpr bool BULK = V < 8 ? V >= 4 : V == 9;
     static constexpr int T = at_least_32(raw_threads(N, W, VT::BUD));
     typedef typename CT<real>::t cplx;
     static constexpr size_t smem = sizeof(cplx) * (size_t)(N + N * W);
