@@ -67,9 +67,10 @@ enum dns_status {
 };
 
 /* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 8, 12,
- * 16, 24, 32, 36, 48, 64, 72, 96, 128, 144, 192, 256, 288, 384, 512, 576,
- * 768, 1024, i.e. the multiples of 4 from 8 to 1024 whose odd part is 1, 3
- * or 9 (transform stages of radix 3 and powers of two); any other N is
+ * 16, 24, 32, 36, 48, 64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384,
+ * 432, 512, 576, 768, 864, 1024, i.e. the multiples of 4 from 8 to 1024
+ * whose odd part is 1, 3, 9 or 27 (transform stages of radix 3 and powers of
+ * two); any other N is
  * DNS_ERR_UNSUPPORTED.  nu > 0 viscosity, dt > 0 time step.
  * cuda_stream: a cudaStream_t to run on, or NULL for a stream the handle
  * creates.  The velocity starts at zero, t = 0, step = 0.

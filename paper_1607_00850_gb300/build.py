@@ -25,7 +25,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdns.so")
 LIB_CHECKED = os.path.join(HERE, "libdns_checked.so")
 
-SIZES = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 128, 144, 192, 256, 288, 384, 512, 576, 768, 1024)
+SIZES = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384, 432, 512, 576, 768, 864, 1024)
 CHECKED_SIZES = (16, 24, 36, 64, 96, 128, 256, 512, 1024)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -46,7 +46,7 @@ def kept_mask(N):
 
 
 # ---------------------------------------------------------------- right-hand side
-@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 36, 48, 64, 72, 96])
+@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 108])
 @pytest.mark.parametrize("dtype", DTYPES, ids=DNAME.get)
 def test_rhs_matches_oracle(dns, orc, N, dtype):
     nu = 0.013
@@ -129,7 +129,7 @@ def test_rhs_matches_oracle_larger_meshes_tuned(dns, orc, N):
     assert rel(got, ref) < TOL[0]
 
 
-@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (768, 0), (1024, 0)])
+@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (768, 0), (864, 0), (1024, 0)])
 def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
     # the bench's launch configuration (autotuned plan); TG's RHS is known
     # mode by mode from 8^3
