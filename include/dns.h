@@ -66,11 +66,11 @@ enum dns_status {
     DNS_ERR_INDEX = 8        /* index-checked build: a kernel met an address outside every buffer */
 };
 
-/* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 8, 12,
- * 16, 24, 32, 36, 48, 64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384,
- * 432, 512, 576, 768, 864, 1024, i.e. the multiples of 4 from 8 to 1024
- * whose odd part is 1, 3, 9 or 27 (transform stages of radix 3 and powers of
- * two); any other N is
+/* Create a solver for an N^3 box.  N: one of the compiled mesh sizes 6, 8,
+ * 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 108, 128, 144, 162, 192, 216,
+ * 256, 288, 324, 384, 432, 486, 512, 576, 648, 768, 864, 972, 1024, i.e.
+ * every even N = 2^a 3^b from 6 to 1024 (transform stages of radix 3 and
+ * powers of two); any other N is
  * DNS_ERR_UNSUPPORTED.  nu > 0 viscosity, dt > 0 time step.
  * cuda_stream: a cudaStream_t to run on, or NULL for a stream the handle
  * creates.  The velocity starts at zero, t = 0, step = 0.

@@ -25,7 +25,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libdns.so")
 LIB_CHECKED = os.path.join(HERE, "libdns_checked.so")
 
-SIZES = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384, 432, 512, 576, 768, 864, 1024)
+SIZES = (6, 8, 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 108, 128, 144, 162,
+         192, 216, 256, 288, 324, 384, 432, 486, 512, 576, 648, 768, 864, 972, 1024)
 CHECKED_SIZES = (16, 24, 36, 64, 96, 128, 256, 512, 1024)
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -68,7 +69,9 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False, c
              (os.path.join(CSRC, "dns_noalloc.cu"), os.path.join(bdir, "dns_noalloc.o"), common),
              (os.path.join(CSRC, "dns_les.cu"), os.path.join(bdir, "dns_les.o"), common),
              (os.path.join(CSRC, "dns_peak.cu"), os.path.join(bdir, "dns_peak.o"), common)]
-    for n in SIZES:
+    # the largest meshes' units take longest: start them first, so that the
+    # pool's last wave holds small units
+    for n in sorted(SIZES, reverse=True):
         stub = ("-DDNS_STUB",) if checked and n not in CHECKED_SIZES else ()
         units.append((os.path.join(CSRC, "dns_inst.cu"), os.path.join(bdir, f"dns_inst_{n}.o"),
                       (f"-DDNS_N={n}", *common, *stub)))

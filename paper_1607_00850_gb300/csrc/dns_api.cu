@@ -14,7 +14,9 @@
 #include <vector>
 
 namespace dns {
-#define DNS_SIZES(X) X(8) X(12) X(16) X(24) X(32) X(36) X(48) X(64) X(72) X(96) X(108) X(128) X(144) X(192) X(216) X(256) X(288) X(384) X(432) X(512) X(576) X(768) X(864) X(1024)
+#define DNS_SIZES(X)                                                                                            \
+    X(6) X(8) X(12) X(16) X(18) X(24) X(32) X(36) X(48) X(54) X(64) X(72) X(96) X(108) X(128) X(144) X(162) X(192) \
+        X(216) X(256) X(288) X(324) X(384) X(432) X(486) X(512) X(576) X(648) X(768) X(864) X(972) X(1024)
 #define DNS_DECL(n) bool get_passes_##n(int, PassSet *);
 DNS_SIZES(DNS_DECL)
 #undef DNS_DECL

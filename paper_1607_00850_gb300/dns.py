@@ -24,8 +24,8 @@ DNS_F32, DNS_F64, DNS_F32_ACC64 = 0, 1, 2
 DTYPE_NAMES = {"f32": DNS_F32, "f64": DNS_F64, "f32_acc64": DNS_F32_ACC64}
 STATUS = {0: "DNS_OK", 1: "DNS_ERR_ARG", 2: "DNS_ERR_OOM", 3: "DNS_ERR_CUDA", 4: "DNS_ERR_TIMEOUT",
           5: "DNS_ERR_NONFINITE", 6: "DNS_ERR_UNSUPPORTED", 7: "DNS_ERR_GUARD", 8: "DNS_ERR_INDEX"}
-SUPPORTED_N = (8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 108, 128, 144, 192, 216, 256, 288, 384, 432, 512, 576, 768, 864,
-               1024)
+SUPPORTED_N = (6, 8, 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 108, 128, 144, 162,
+               192, 216, 256, 288, 324, 384, 432, 486, 512, 576, 648, 768, 864, 972, 1024)
 
 # symbol -> (restype, argtypes); the complete exported surface of dns.h
 _vp, _i, _d, _dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.POINTER(ctypes.c_double)

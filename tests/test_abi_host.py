@@ -51,6 +51,8 @@ def test_init_validates_arguments_before_device_work(lib):
     h = ctypes.c_void_p()
     assert lib.dns_init(10, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6   # N not 2^a 3^b
     assert lib.dns_init(40, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
+    assert lib.dns_init(4, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6    # below the smallest mesh
+    assert lib.dns_init(27, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6   # odd
     assert lib.dns_init(2048, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
     assert lib.dns_init(7, 0.01, 0.01, 0, None, ctypes.byref(h)) == 6
     assert lib.dns_init(32, 0.01, 0.01, 3, None, ctypes.byref(h)) == 1   # dtype
@@ -102,11 +104,12 @@ def test_checked_library_builds_and_exports_the_same_boundary():
 def test_supported_sizes_match_plan():
     from paper_1607_00850_gb300 import build, dns
     assert tuple(build.SIZES) == tuple(dns.SUPPORTED_N)
-    for n in dns.SUPPORTED_N:
-        m = n
-        while m % 3 == 0:
-            m //= 3
-        assert m & (m - 1) == 0 and n % 4 == 0
+    # exactly the even N = 2^a 3^b from 6 to 1024
+    def smooth(n):
+        while n % 3 == 0:
+            n //= 3
+        return n & (n - 1) == 0
+    assert list(dns.SUPPORTED_N) == [n for n in range(6, 1025, 2) if smooth(n)]
 
 
 class _FakeDeviceTensor:

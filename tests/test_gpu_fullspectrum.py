@@ -1,6 +1,7 @@
 """Mode-by-mode parity with the FP64 oracle on fields that fill the whole
 kept cube, at every mesh from 128^3 to 576^3 (powers of two and their
-multiples by 3, 9 and 27) and for every compiled variant of every pass.
+multiples by 3, 9, 27, 81 and 243) and for every compiled variant of every
+pass.
 
 The random-isotropic fields of the configured runs put almost all of their
 energy at |k| < 16, so a relative L2 norm over the whole field says little
@@ -73,7 +74,8 @@ def compare(got, ref, tol, mask, what=""):
     return (num / den) ** 0.5
 
 
-@pytest.fixture(scope="module", params=[128, 144, 192, 216, 256, 288, 384, 432, 512, 576], ids=lambda n: f"N{n}")
+@pytest.fixture(scope="module", params=[128, 144, 162, 192, 216, 256, 288, 324, 384, 432, 486, 512, 576],
+                ids=lambda n: f"N{n}")
 def box(request, orc):
     """(N, field on the device as complex128, oracle RHS on the device, kept mask)."""
     N = request.param

@@ -4,9 +4,9 @@ Tolerances: relative L2 over all stored modes, ||gpu - oracle|| / ||oracle||,
 1e-12 for DNS_F64 and 2e-6 for DNS_F32 / DNS_F32_ACC64 per right-hand side;
 kinetic energy within 1e-4 relative after the configured steps in FP32.
 Sizes span several tiles and ragged tails (Kz = K+1 is not a multiple of the
-tile width for N = 32, 64, 256, 512), the smallest (8) and largest (1024)
-supported meshes, and the 512^3 workload in the launch configuration the
-benchmark times.
+tile width for N = 32, 64, 256, 512), the smallest (6) and largest (1024)
+supported meshes, meshes with up to five radix-3 stages, and the 512^3
+workload in the launch configuration the benchmark times.
 """
 import os
 
@@ -46,7 +46,7 @@ def kept_mask(N):
 
 
 # ---------------------------------------------------------------- right-hand side
-@pytest.mark.parametrize("N", [8, 12, 16, 24, 32, 36, 48, 64, 72, 96, 108])
+@pytest.mark.parametrize("N", [6, 8, 12, 16, 18, 24, 32, 36, 48, 54, 64, 72, 96, 108])
 @pytest.mark.parametrize("dtype", DTYPES, ids=DNAME.get)
 def test_rhs_matches_oracle(dns, orc, N, dtype):
     nu = 0.013
@@ -129,7 +129,7 @@ def test_rhs_matches_oracle_larger_meshes_tuned(dns, orc, N):
     assert rel(got, ref) < TOL[0]
 
 
-@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (768, 0), (864, 0), (1024, 0)])
+@pytest.mark.parametrize("N,dtype", [(512, 0), (512, 2), (648, 0), (768, 0), (864, 0), (972, 0), (1024, 0)])
 def test_rhs_taylor_green_at_full_size(dns, orc, N, dtype):
     # the bench's launch configuration (autotuned plan); TG's RHS is known
     # mode by mode from 8^3
