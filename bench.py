@@ -209,7 +209,7 @@ def unpruned_step_bytes(N, dtype):
     return 216 * N * N * (N // 2 + 1) * cr
 
 
-FUSED_P5_FROM = 8  # plan[4] values from here on select a fused x-forward + update variant
+FUSED_P5_FROM = 10  # plan[4] values from here on select a fused x-forward + update variant (PassSet::NCOLV)
 
 
 def step_launches(plan) -> int:

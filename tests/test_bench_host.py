@@ -117,4 +117,14 @@ def test_step_flops_grow_as_n3_log_n():
 def test_step_launch_count_follows_the_plan():
     assert bench.step_launches([7, 7, 9, 3, 0]) == 24
     assert bench.step_launches([7, 7, 9, 3, 7]) == 24
+    assert bench.step_launches([9, 9, 14, 8, 9]) == 24  # half-width column variants
     assert bench.step_launches([7, 7, 9, 3, bench.FUSED_P5_FROM]) == 20
+
+
+def test_fused_variant_offset_matches_the_library():
+    # plan[4] >= NCOLV selects a fused x-forward + update variant in the
+    # library (dns_api.cu); bench.py counts launches with the same offset
+    import re
+    with open(os.path.join(ROOT, "paper_1607_00850_gb300", "csrc", "dns_internal.h")) as f:
+        ncolv = int(re.search(r"NCOLV\s*=\s*(\d+)", f.read()).group(1))
+    assert bench.FUSED_P5_FROM == ncolv
