@@ -28,7 +28,6 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RK4 grid-point-steps/s at 512^3, FP32 vs FP64, % of HBM roofline"
-SEED = 2024
 
 
 def parse():
@@ -48,16 +47,17 @@ def parse():
 
 
 def workload(N):
-    from paper_1607_00850_gb300 import inputs
-    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
-    dt = inputs.cfl_dt(uh, 0.5)
-    return uh, 1.0 / 4000.0, dt
+    """(initial field, nu, dt) of the decaying-turbulence benchmark at N^3."""
+    from paper_1607_00850_gb300 import configs
+    cfg = configs.DECAYING_512
+    uh = cfg.initial_field(N)
+    return uh, cfg.nu, cfg.time_step(uh)
 
 
 def config(N, dt):
-    return {"workload": f"decaying isotropic turbulence {N}^3, E(k)~k^4 exp(-2(k/4)^2), unit energy, "
-                        f"nu=1/4000, CFL-0.5 dt, 2/3 dealiasing, classical RK4",
-            "N": N, "nu": 1.0 / 4000.0, "dt": dt, "seed": SEED,
+    from paper_1607_00850_gb300 import configs
+    cfg = configs.DECAYING_512
+    return {"workload": cfg.describe(N), "N": N, "nu": cfg.nu, "dt": dt, "seed": cfg.seed,
             "l2": "inputs larger than L2 (working set several GB); no flush"}
 
 
@@ -416,10 +416,11 @@ def ensemble_bench(args, stream):
     per-box k0 ~ U[2,6] and nu ~ U[0.005, 0.02]) timed over K graph-replayed
     RK4 steps of all boxes."""
     import torch
-    from paper_1607_00850_gb300 import dns, inputs
-    params = inputs.ensemble_params(64, 16)
+    from paper_1607_00850_gb300 import configs, dns, inputs
+    cfg = configs.ENSEMBLE
+    params = cfg.params()
     Ns = [p[0] for p in params]
-    e = dns.Ensemble(Ns, [p[2] for p in params], 0.005, dns.DNS_F32, stream=stream.cuda_stream)
+    e = dns.Ensemble(Ns, [p[2] for p in params], cfg.dt, cfg.dtype, stream=stream.cuda_stream)
     for b, (Nb, k0, nub, seed) in enumerate(params):
         e.set_velocity(b, inputs.random_isotropic(Nb, seed=seed, k0=k0).astype(np.complex64))
     dns.dns_ensemble_autotune(e.h)
@@ -436,7 +437,7 @@ def ensemble_bench(args, stream):
     pts = float(sum(n ** 3 for n in Ns))
     step_bytes = sum(sum(sum(pass_bytes(n, 0, st)) for st in range(4)) for n in Ns)
     peak, src = measured_peaks()
-    return {"workload": "64 boxes at 64^3 + 16 boxes at 96^3, FP32, dt=0.005, 2/3 dealiasing, RK4",
+    return {"workload": cfg.describe(),
             "value": pts * args.steps / (ms / 1e3), "unit": "grid-point-steps/s",
             "ms_per_step": ms / args.steps, "steps": args.steps,
             "step_bytes_pruned": step_bytes,
@@ -483,9 +484,9 @@ def cpu_baseline(N, nu):
     """The FP64 oracle, as it stands, on the host cores: one right-hand side
     evaluation (a quarter of an RK4 step) on the same field."""
     import oracle
-    from paper_1607_00850_gb300 import inputs
+    from paper_1607_00850_gb300 import configs
     o = oracle.load()
-    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
+    uh = configs.DECAYING_512.initial_field(N)
     t0 = time.perf_counter()
     o.rhs(uh, nu)
     t = time.perf_counter() - t0
@@ -501,12 +502,13 @@ def run_reference(args, rank, world):
     within two minutes (at least one).  `steps` and `warmup` report the RK4
     steps actually done, so steps * ms_per_step is the timed region."""
     import oracle
-    from paper_1607_00850_gb300 import inputs
+    from paper_1607_00850_gb300 import configs, inputs
     o = oracle.load()
     N = args.N
-    nu = 1.0 / 4000.0
-    uh = inputs.random_isotropic(N, seed=SEED, k0=4.0)
-    dt = inputs.cfl_dt(uh, 0.5)
+    cfg = configs.DECAYING_512
+    nu = cfg.nu
+    uh = cfg.initial_field(N)
+    dt = cfg.time_step(uh)
     o.rk4(inputs.random_isotropic(32, seed=1), 1e-3, 1e-3, 1)   # warm the code once, small
     u = uh
     warm, tw = 0, time.perf_counter()

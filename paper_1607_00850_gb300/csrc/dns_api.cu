@@ -13,6 +13,20 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// A named NVTX range for the duration of an entry point: a timeline tool
+// (Nsight Systems or ncu's NVTX filters) shows each C-ABI call; with no tool
+// attached the push and pop do nothing.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+}  // namespace
+
 namespace dns {
 #define DNS_SIZES(X)                                                                                            \
     X(6) X(8) X(12) X(16) X(18) X(24) X(32) X(36) X(48) X(54) X(64) X(72) X(96) X(108) X(128) X(144) X(162) X(192) \
@@ -561,6 +575,7 @@ static int poll_device_status(dns_ctx *h) {
 }
 
 int dns_synchronize(dns_handle h) {
+    TraceRange trace_("dns_synchronize");
     if (!h) return DNS_ERR_ARG;
     CK(cudaStreamSynchronize(h->stream));
     if (h->s_in) CK(cudaStreamSynchronize(h->s_in));
@@ -682,6 +697,7 @@ static int ensure_async_io(dns_ctx *h) {
 extern "C" {
 
 int dns_set_velocity_async(dns_handle h, const void *uhat) {
+    TraceRange trace_("dns_set_velocity_async");
     if (!h || !uhat) return DNS_ERR_ARG;
     const int rc = ensure_async_io(h);
     if (rc != DNS_OK) return rc;
@@ -698,6 +714,7 @@ int dns_set_velocity_async(dns_handle h, const void *uhat) {
 }
 
 int dns_get_velocity_async(dns_handle h, void *uhat) {
+    TraceRange trace_("dns_get_velocity_async");
     if (!h || !uhat) return DNS_ERR_ARG;
     const int rc = ensure_async_io(h);
     if (rc != DNS_OK) return rc;
@@ -715,11 +732,13 @@ int dns_get_velocity_async(dns_handle h, void *uhat) {
 }
 
 int dns_set_velocity(dns_handle h, const void *uhat, int on_device) {
+    TraceRange trace_("dns_set_velocity");
     if (!h || !uhat) return DNS_ERR_ARG;
     return set_state(h, 0, uhat, on_device);
 }
 
 int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
+    TraceRange trace_("dns_set_velocity_physical");
     if (!h || !u) return DNS_ERR_ARG;
     const size_t nreal = 3ull * h->N * h->N * h->N;
     const size_t bytes = nreal * (h->cio / 2);
@@ -752,11 +771,13 @@ int dns_set_velocity_physical(dns_handle h, const void *u, int on_device) {
 }
 
 int dns_get_velocity(dns_handle h, void *uhat, int on_device) {
+    TraceRange trace_("dns_get_velocity");
     if (!h || !uhat) return DNS_ERR_ARG;
     return get_state(h, 0, uhat, on_device);
 }
 
 int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
+    TraceRange trace_("dns_rhs");
     if (!h || !uhat_in || !duhat_out) return DNS_ERR_ARG;
     const size_t bytes = 3ull * h->N * h->N * (h->N / 2 + 1) * h->cio;
     const void *src = uhat_in;
@@ -793,6 +814,7 @@ int dns_rhs(dns_handle h, const void *uhat_in, void *duhat_out, int on_device) {
 }
 
 int dns_step(dns_handle h, int n) {
+    TraceRange trace_("dns_step");
     if (!h || n < 0) return DNS_ERR_ARG;
     if (n == 0) return DNS_OK;
     if (!h->exec) {
@@ -823,6 +845,7 @@ int dns_step(dns_handle h, int n) {
 }
 
 int dns_step_profiled(dns_handle h, int n, double *pass_ms, double *total_ms) {
+    TraceRange trace_("dns_step_profiled");
     if (!h || n < 0 || !pass_ms) return DNS_ERR_ARG;
     for (int i = 0; i < DNS_NPASS; ++i) pass_ms[i] = 0.0;
     if (total_ms) *total_ms = 0.0;
@@ -1083,6 +1106,7 @@ static int autotune_ctx(dns_ctx *h, const char *cache_path, int reps) {
 extern "C" {
 
 int dns_autotune(dns_handle h, const char *cache_path, int *plan_out) {
+    TraceRange trace_("dns_autotune");
     if (!h) return DNS_ERR_ARG;
     int rc = autotune_ctx(h, cache_path, 3);
     if (!rc && plan_out)
@@ -1252,6 +1276,7 @@ int dns_ensemble_get_velocity(dns_ensemble e, int box, void *uhat, int on_device
 }
 
 int dns_ensemble_step(dns_ensemble e, int n) {
+    TraceRange trace_("dns_ensemble_step");
     if (!e || n < 0) return DNS_ERR_ARG;
     if (n == 0) return DNS_OK;
     if (!e->exec) {

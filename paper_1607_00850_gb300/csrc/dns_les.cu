@@ -24,6 +24,20 @@
 #include <new>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
+namespace {
+// A named NVTX range for the duration of an entry point: a timeline tool
+// (Nsight Systems or ncu's NVTX filters) shows each C-ABI call; with no tool
+// attached the push and pop do nothing.
+struct TraceRange {
+    explicit TraceRange(const char *name) { nvtxRangePushA(name); }
+    ~TraceRange() { nvtxRangePop(); }
+    TraceRange(const TraceRange &) = delete;
+    TraceRange &operator=(const TraceRange &) = delete;
+};
+}  // namespace
+
 namespace dns {
 namespace les {
 
@@ -1202,6 +1216,7 @@ int dns_net_set_params(dns_net net, const float *host, long count) {
 }
 
 int dns_net_forward(dns_net net, const float *g, float *tau) {
+    TraceRange trace_("dns_net_forward");
     if (!net || !g || !tau) return DNS_ERR_ARG;
     const long long V = (long long)net->n * net->n * net->n;
     NK(net_forward(net, g, net->stream));
@@ -1255,6 +1270,7 @@ int dns_net_forward_profiled(dns_net net, const float *g, float *tau, int reps, 
 }
 
 int dns_net_gradients(dns_net net, const float *g, const float *tau, double *loss, float *grad_host, long count) {
+    TraceRange trace_("dns_net_gradients");
     if (!net || !g || !tau || (grad_host && count != NET_PARAMS)) return DNS_ERR_ARG;
     NK(cudaMemsetAsync(net->gw1, 0, sizeof(float) * 32 * 27 * 16, net->stream));
     NK(cudaMemsetAsync(net->gw2, 0, sizeof(float) * 32 * 27 * 32, net->stream));
@@ -1292,6 +1308,7 @@ int dns_net_gradients(dns_net net, const float *g, const float *tau, double *los
 }
 
 int dns_net_train_step(dns_net net, int nsamples, const float *g, const float *tau, double lr, double *loss) {
+    TraceRange trace_("dns_net_train_step");
     if (!net || !g || !tau || nsamples < 1 || !(lr > 0.0)) return DNS_ERR_ARG;
     const long long V = (long long)net->n * net->n * net->n;
     NK(cudaMemsetAsync(net->gw1, 0, sizeof(float) * 32 * 27 * 16, net->stream));
@@ -1458,6 +1475,7 @@ int dns_les_builder_free(dns_les_builder b) {
 }
 
 int dns_les_builder_run(dns_les_builder b, dns_handle dns, float *g, float *tau, void *ubar_hat) {
+    TraceRange trace_("dns_les_builder_run");
     if (!b || !dns || !g || !tau) return DNS_ERR_ARG;
     dns::InternalView v;
     if (dns::internal_view(dns, &v) || v.N != b->N) return DNS_ERR_ARG;

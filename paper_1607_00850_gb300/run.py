@@ -19,7 +19,11 @@ import os
 import sys
 import time
 
-from . import checkpoint, inputs
+from . import checkpoint, configs, inputs
+
+# defaults of the flags a configuration may set (None in the parser, so that
+# a flag given on the command line overrides the configuration's value)
+_DEFAULTS = {"N": 128, "nu": 1.0 / 1600.0, "dt": 1e-3, "steps": 1000, "init": "tg", "seed": 2024, "k0": 4.0}
 
 
 def initial_field(kind: str, N: int, seed: int, k0: float):
@@ -28,6 +32,23 @@ def initial_field(kind: str, N: int, seed: int, k0: float):
     if kind == "isotropic":
         return inputs.random_isotropic(N, seed=seed, k0=k0)
     raise ValueError(f"unknown initial condition {kind!r}")
+
+
+def resolve_config(a) -> None:
+    """Fill the flags left unset: from --config if given, else the defaults.
+    A configuration with a CFL rule gets its dt from its initial field."""
+    cfg = configs.ALL[a.config] if getattr(a, "config", None) else None
+    if cfg is not None:
+        given = {"N": cfg.N, "nu": cfg.nu, "steps": cfg.steps, "seed": cfg.seed, "k0": cfg.k0,
+                 "init": "tg" if cfg.init == "taylor_green" else "isotropic"}
+        for k, v in given.items():
+            if getattr(a, k) is None:
+                setattr(a, k, v)
+        if a.dt is None:
+            a.dt = cfg.time_step(initial_field(a.init, a.N, a.seed, a.k0)) if cfg.dt is None else cfg.dt
+    for k, v in _DEFAULTS.items():
+        if getattr(a, k) is None:
+            setattr(a, k, v)
 
 
 def diagnostics(solver, spectrum: bool) -> dict:
@@ -75,15 +96,18 @@ def run(solver, steps: int, every: int, log, ckpt_path=None, ckpt_every: int = 0
 
 def main(argv=None) -> int:
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
-    p.add_argument("--N", type=int, default=128)
+    p.add_argument("--config", choices=sorted(n for n, c in configs.ALL.items() if isinstance(c, configs.DNSConfig)),
+                   default=None, help="take N, nu, dt (fixed or CFL), steps and the initial field from a "
+                                      "configured workload; flags given as well override it")
+    p.add_argument("--N", type=int, default=None)
     p.add_argument("--dtype", choices=["f32", "f64", "f32_acc64"], default="f32")
-    p.add_argument("--nu", type=float, default=1.0 / 1600.0)
-    p.add_argument("--dt", type=float, default=1e-3)
-    p.add_argument("--steps", type=int, default=1000, help="step count to reach")
+    p.add_argument("--nu", type=float, default=None)
+    p.add_argument("--dt", type=float, default=None)
+    p.add_argument("--steps", type=int, default=None, help="step count to reach")
     p.add_argument("--every", type=int, default=100)
-    p.add_argument("--init", choices=["tg", "isotropic"], default="tg")
-    p.add_argument("--seed", type=int, default=2024)
-    p.add_argument("--k0", type=float, default=4.0)
+    p.add_argument("--init", choices=["tg", "isotropic"], default=None)
+    p.add_argument("--seed", type=int, default=None)
+    p.add_argument("--k0", type=float, default=None)
     p.add_argument("--ifrk4", action="store_true", help="integrating-factor RK4")
     p.add_argument("--spectrum", action="store_true")
     p.add_argument("--log", default="-")
@@ -93,6 +117,7 @@ def main(argv=None) -> int:
     p.add_argument("--allow-parameter-change", action="store_true",
                    help="resume with --nu/--dt/--ifrk4 that differ from the checkpoint's")
     a = p.parse_args(argv)
+    resolve_config(a)
     from . import dns
     dtype = dns.DTYPE_NAMES[a.dtype]
     log = sys.stdout if a.log == "-" else open(a.log, "a" if a.resume else "w")

@@ -22,7 +22,7 @@ the per-step and energy bars).
 import numpy as np
 import pytest
 
-from paper_1607_00850_gb300 import inputs
+from paper_1607_00850_gb300 import configs, inputs
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -91,18 +91,17 @@ def run_against_oracle(dns, orc, uh, N, nu, dt, nsteps, dtypes, tuned):
 
 @pytest.mark.slow
 def test_decaying_turbulence_256_fifty_steps_fp32_and_fp64(dns, orc):
-    N, nu, dt = 256, 1e-3, 0.002
-    uh = inputs.random_isotropic(N, seed=2024, k0=4.0)
-    worst = run_against_oracle(dns, orc, uh, N, nu, dt, 50, (0, 1), tuned=True)
+    c = configs.DECAYING_256  # 256^3, nu = 1e-3, dt = 0.002, 50 steps, FP32 and FP64
+    uh = c.initial_field()
+    worst = run_against_oracle(dns, orc, uh, c.N, c.nu, c.time_step(), c.steps, c.dtypes, tuned=True)
     assert worst[1] <= 1e-12 and worst[0] <= 1e-4
 
 
 @pytest.mark.slow
 def test_benchmark_field_512_two_cfl_steps(dns, orc):
-    N, nu = 512, 1.0 / 4000
-    uh = inputs.random_isotropic(N, seed=2024, k0=4.0)
-    dt = inputs.cfl_dt(uh, 0.5)
-    run_against_oracle(dns, orc, uh, N, nu, dt, 2, (0, 2, 1), tuned=True)
+    c = configs.DECAYING_512  # the benchmark's field, nu = 1/4000, CFL-0.5 dt
+    uh = c.initial_field()
+    run_against_oracle(dns, orc, uh, c.N, c.nu, c.time_step(uh), 2, (0, 2, 1), tuned=True)
 
 
 @pytest.mark.parametrize("N,dt", [(32, 0.01), (64, 0.005)])
