@@ -156,3 +156,31 @@ def test_noalloc_wrapper_rejects_mismatched_buffers():
                     _FakeDeviceTensor(torch.float64, 2, device="cuda:1")):       # other device
         with pytest.raises(ValueError, match="out"):
             dns.dns_energy_noalloc(N, dns.DNS_F32, good32, 0.01, out=bad_out)
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(lib, tmp_path):
+    # the boundary is a C ABI: include/dns.h compiles as pedantic C99 and a
+    # C program links against libdns.so and gets the documented statuses
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "abi.c"
+    src.write_text(
+        '#include "dns.h"\n'
+        "int main(void) {\n"
+        "    dns_handle h = 0;\n"
+        "    double E = 0.0;\n"
+        "    if (dns_energy(h, &E) != DNS_ERR_ARG) return 1;\n"
+        "    if (dns_init(10, 0.01, 0.01, DNS_F32, 0, &h) != DNS_ERR_UNSUPPORTED || h) return 2;\n"
+        "    if (dns_checked_build() != 0) return 3;\n"
+        "    return dns_strerror(DNS_ERR_INDEX)[0] ? 0 : 4;\n"
+        "}\n")
+    libdir = os.path.join(ROOT, "paper_1607_00850_gb300")
+    exe = tmp_path / "abi"
+    r = subprocess.run([cc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                        str(src), "-L", libdir, "-ldns", f"-Wl,-rpath,{libdir}", "-o", str(exe)],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    assert subprocess.run([str(exe)]).returncode == 0
